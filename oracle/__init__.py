@@ -1,0 +1,314 @@
+"""CPU oracle for colour-class-parallel heat-bath Glauber dynamics.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark are the only callers.  The library product never imports
+this package, and this package imports nothing from the product.
+
+Thin ctypes wrapper over ``oracle.c`` (plain single-threaded C).  Every
+function documents the passage of Keating & Sridhar, "Random Tilings with the
+GPU", that it follows.  States are numpy uint8 arrays in the canonical layout
+``[plane, y, x]`` described in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+DOMINO, LOZENGE, SIXV = "domino", "lozenge", "sixv"
+PASSES = {DOMINO: 2, LOZENGE: 3, SIXV: 4}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc into liboracle.so next to it."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-fvisibility=hidden", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u8p, u32p, u64p, i32p, dp = (ctypes.c_void_p,) * 5
+        c = ctypes
+        sig = {
+            "or_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "or_site_u": (c.c_uint32, [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64]),
+            "or_splitmix64": (c.c_uint64, [c.c_uint64]),
+            "or_state_hash": (c.c_uint64, [u8p, c.c_uint64]),
+            "or_domino_aztec_init": (c.c_int, [c.c_int, u8p]),
+            "or_domino_rect_init": (c.c_int, [c.c_int, c.c_int, u8p]),
+            "or_domino_site_states": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
+            "or_domino_apply_pass": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
+            "or_domino_sweeps": (c.c_int, [u8p, c.c_int, c.c_int, u32p, c.c_uint32, c.c_uint64,
+                                           c.c_uint32, c.c_uint64, c.c_uint64, u64p]),
+            "or_domino_thresholds": (None, [dp, c.c_int, c.c_int, u32p]),
+            "or_domino_weight": (c.c_double, [u8p, c.c_int, c.c_int, dp]),
+            "or_domino_check": (c.c_int64, [u8p, c.c_int, c.c_int, u8p]),
+            "or_domino_height": (c.c_int64, [u8p, c.c_int, c.c_int, i32p]),
+            "or_lozenge_hexagon_init": (c.c_int, [c.c_int, c.c_int, c.c_int, u8p]),
+            "or_lozenge_site_states": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
+            "or_lozenge_apply_pass": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
+            "or_lozenge_sweeps": (c.c_int, [u8p, c.c_int, c.c_int, u32p, c.c_uint32, c.c_uint64,
+                                            c.c_uint32, c.c_uint64, c.c_uint64, u64p]),
+            "or_lozenge_thresholds": (c.c_int, [c.c_double, u32p, u32p]),
+            "or_lozenge_check": (c.c_int64, [u8p, c.c_int, c.c_int, u8p, u8p]),
+            "or_lozenge_height": (c.c_int64, [u8p, c.c_int, c.c_int, i32p]),
+            "or_sixv_dwbc_init": (c.c_int, [c.c_int, u8p]),
+            "or_sixv_vertex_type": (c.c_int, [u8p, c.c_int, c.c_int, c.c_int]),
+            "or_sixv_check_dwbc": (c.c_int64, [u8p, c.c_int]),
+            "or_sixv_site_states": (None, [u8p, c.c_int, c.c_int, u8p]),
+            "or_sixv_apply_pass": (None, [u8p, c.c_int, c.c_int, u8p]),
+            "or_sixv_sweeps": (c.c_int, [u8p, c.c_int, u32p, c.c_uint64, c.c_uint32, c.c_uint64,
+                                         c.c_uint64, u64p]),
+            "or_sixv_weight": (c.c_double, [u8p, c.c_int, dp]),
+            "or_sixv_thresholds": (c.c_int, [dp, u32p]),
+            "or_sixv_height": (c.c_int64, [u8p, c.c_int, i32p]),
+            "or_accumulate": (None, [u8p, c.c_uint64, u32p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------------------
+# Random numbers
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 (Salmon et al., SC'11) of a 4-word counter and 2-word key."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def site_u(seed: int, stream: int, sweep: int, pass_: int, rank: int) -> int:
+    """The 32-bit uniform of one site, bit-plane keyed (module docstring of oracle.c)."""
+    return int(lib().or_site_u(seed, stream, sweep, pass_, rank))
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(x))
+
+
+def state_hash(st: np.ndarray) -> int:
+    """Order-independent 64-bit hash of a canonical state."""
+    st = np.ascontiguousarray(st, dtype=np.uint8)
+    return int(lib().or_state_hash(_p(st), st.size))
+
+
+# --------------------------------------------------------------------------
+# Domains and initial states
+# --------------------------------------------------------------------------
+def aztec(n: int) -> np.ndarray:
+    """Aztec diamond of order n, all-horizontal tiling; shape (2, 2n+1, 2n+1)."""
+    W = 2 * n + 1
+    st = np.zeros((2, W, W), dtype=np.uint8)
+    lib().or_domino_aztec_init(n, _p(st))
+    return st
+
+
+def rect(w: int, h: int) -> np.ndarray:
+    """w x h faces; all-horizontal (w even) or all-vertical (h even)."""
+    st = np.zeros((2, h + 1, w + 1), dtype=np.uint8)
+    if lib().or_domino_rect_init(w, h, _p(st)) != 0:
+        raise ValueError("rectangle %dx%d has no domino tiling" % (w, h))
+    return st
+
+
+def hexagon(a: int, b: int, c: int) -> np.ndarray:
+    """a x b x c hexagon, empty-box tiling; shape (3, b+c+1, a+c+1)."""
+    st = np.zeros((3, b + c + 1, a + c + 1), dtype=np.uint8)
+    lib().or_lozenge_hexagon_init(a, b, c, _p(st))
+    return st
+
+
+def dwbc(N: int) -> np.ndarray:
+    """Six-vertex domain-wall boundary, identity start; shape (2, N+2, N+2)."""
+    st = np.zeros((2, N + 2, N + 2), dtype=np.uint8)
+    lib().or_sixv_dwbc_init(N, _p(st))
+    return st
+
+
+def lattice_of(st: np.ndarray, hint: str | None = None) -> str:
+    if hint:
+        return hint
+    return LOZENGE if st.shape[0] == 3 else DOMINO
+
+
+# --------------------------------------------------------------------------
+# Moves
+# --------------------------------------------------------------------------
+def site_states(lattice: str, st: np.ndarray, pass_: int) -> np.ndarray:
+    """Per site of class `pass_`: 0 not rotatable, 1 DOWN, 2 UP; shape (H, W)."""
+    _, H, W = st.shape
+    out = np.zeros((H, W), dtype=np.uint8)
+    L = lib()
+    if lattice == DOMINO:
+        L.or_domino_site_states(_p(st), W, H, pass_, _p(out))
+    elif lattice == LOZENGE:
+        L.or_lozenge_site_states(_p(st), W, H, pass_, _p(out))
+    else:
+        L.or_sixv_site_states(_p(st), W - 2, pass_, _p(out))
+    return out
+
+
+def apply_pass(lattice: str, st: np.ndarray, pass_: int, dec: np.ndarray) -> None:
+    """Cluster move on class `pass_`: rotatable sites go UP where dec=1 (in place)."""
+    _, H, W = st.shape
+    dec = np.ascontiguousarray(dec, dtype=np.uint8)
+    L = lib()
+    if lattice == DOMINO:
+        L.or_domino_apply_pass(_p(st), W, H, pass_, _p(dec))
+    elif lattice == LOZENGE:
+        L.or_lozenge_apply_pass(_p(st), W, H, pass_, _p(dec))
+    else:
+        L.or_sixv_apply_pass(_p(st), W - 2, pass_, _p(dec))
+
+
+def sweeps(lattice: str, st: np.ndarray, *, seed: int, stream: int = 0, sweep0: int = 0,
+           k: int = 1, t_scalar: int | None = None, t_site: np.ndarray | None = None,
+           t16: np.ndarray | None = None, want_hashes: bool = False):
+    """Run k heat-bath sweeps in place (Eq. 1.1 with colour-class clusters).
+
+    Domino / lozenge: threshold t_site ([H, W] uint32) or t_scalar.  Six-vertex:
+    the 16-entry table t16.  Returns the per-sweep hashes if asked.
+    """
+    _, H, W = st.shape
+    assert st.dtype == np.uint8 and st.flags["C_CONTIGUOUS"]
+    hashes = np.zeros(max(k, 1), dtype=np.uint64) if want_hashes else None
+    hp = _p(hashes) if hashes is not None else None
+    L = lib()
+    if lattice in (DOMINO, LOZENGE):
+        ts = None
+        if t_site is not None:
+            ts = np.ascontiguousarray(t_site, dtype=np.uint32)
+            assert ts.shape == (H, W)
+        tsc = 0 if t_scalar is None else int(t_scalar)
+        fn = L.or_domino_sweeps if lattice == DOMINO else L.or_lozenge_sweeps
+        rc = fn(_p(st), W, H, _p(ts) if ts is not None else None, tsc, seed, stream, sweep0, k, hp)
+    else:
+        t = np.ascontiguousarray(t16, dtype=np.uint32)
+        assert t.shape == (16,)
+        rc = L.or_sixv_sweeps(_p(st), W - 2, _p(t), seed, stream, sweep0, k, hp)
+    if rc != 0:
+        raise MemoryError("oracle sweep failed")
+    return hashes[:k] if want_hashes else None
+
+
+# --------------------------------------------------------------------------
+# Thresholds and weights
+# --------------------------------------------------------------------------
+def domino_thresholds(w: np.ndarray) -> np.ndarray:
+    """t = floor(2^32 wE wW / (wE wW + wN wS)) per vertex (Sec. 1.1.1)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _, H, W = w.shape
+    t = np.zeros((H, W), dtype=np.uint32)
+    lib().or_domino_thresholds(_p(w), W, H, _p(t))
+    return t
+
+
+def domino_weight(st: np.ndarray, w: np.ndarray) -> float:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _, H, W = st.shape
+    return float(lib().or_domino_weight(_p(st), W, H, _p(w)))
+
+
+def lozenge_thresholds(q: float):
+    ta = np.zeros(1, dtype=np.uint32)
+    tr = np.zeros(1, dtype=np.uint32)
+    if lib().or_lozenge_thresholds(q, _p(ta), _p(tr)) != 0:
+        raise ValueError("q too small")
+    return int(ta[0]), int(tr[0])
+
+
+def sixv_thresholds(w6) -> np.ndarray:
+    w = np.ascontiguousarray(w6, dtype=np.float64)
+    t = np.zeros(16, dtype=np.uint32)
+    if lib().or_sixv_thresholds(_p(w), _p(t)) != 0:
+        raise ValueError("bad six-vertex table")
+    return t
+
+
+def sixv_weight(st: np.ndarray, w6) -> float:
+    w = np.ascontiguousarray(w6, dtype=np.float64)
+    return float(lib().or_sixv_weight(_p(st), st.shape[1] - 2, _p(w)))
+
+
+def sixv_vertex_type(st: np.ndarray, X: int, Y: int) -> int:
+    return int(lib().or_sixv_vertex_type(_p(st), st.shape[1] - 2, X, Y))
+
+
+# --------------------------------------------------------------------------
+# Invariants and observables
+# --------------------------------------------------------------------------
+def domino_check(st: np.ndarray, face_mask: np.ndarray | None = None) -> int:
+    _, H, W = st.shape
+    fm = None
+    if face_mask is not None:
+        fm = np.ascontiguousarray(face_mask, dtype=np.uint8)
+        assert fm.shape == (H - 1, W - 1)
+    return int(lib().or_domino_check(_p(st), W, H, _p(fm) if fm is not None else None))
+
+
+def lozenge_check(st: np.ndarray, up_mask=None, dn_mask=None) -> int:
+    _, H, W = st.shape
+    um = np.ascontiguousarray(up_mask, dtype=np.uint8) if up_mask is not None else None
+    dm = np.ascontiguousarray(dn_mask, dtype=np.uint8) if dn_mask is not None else None
+    return int(lib().or_lozenge_check(_p(st), W, H, _p(um) if um is not None else None,
+                                      _p(dm) if dm is not None else None))
+
+
+def sixv_check_dwbc(st: np.ndarray) -> int:
+    return int(lib().or_sixv_check_dwbc(_p(st), st.shape[1] - 2))
+
+
+HEIGHT_NONE = np.iinfo(np.int32).min
+
+
+def height(lattice: str, st: np.ndarray):
+    """Height function (domino Fig. 2, lozenge cube stack, six-vertex Fig. 6).
+
+    Returns (h, inconsistencies).  Domino / lozenge: int32 [H, W] on vertices,
+    HEIGHT_NONE off the domain.  Six-vertex: int32 [N+1, N+1] on faces.
+    """
+    _, H, W = st.shape
+    L = lib()
+    if lattice == SIXV:
+        N = W - 2
+        h = np.zeros((N + 1, N + 1), dtype=np.int32)
+        bad = L.or_sixv_height(_p(st), N, _p(h))
+    else:
+        h = np.zeros((H, W), dtype=np.int32)
+        fn = L.or_domino_height if lattice == DOMINO else L.or_lozenge_height
+        bad = fn(_p(st), W, H, _p(h))
+    return h, int(bad)
+
+
+def accumulate(st: np.ndarray, counts: np.ndarray) -> None:
+    """Edge-occupancy counters: counts += st (uint32, same shape)."""
+    assert counts.dtype == np.uint32 and counts.shape == st.shape
+    lib().or_accumulate(_p(st), st.size, _p(counts))
