@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput benchmark: uniform domino tilings of the Aztec diamond of order
+2048 (8,384,513 flip attempts per sweep), all-horizontal start, seed 7,
+10^5 heat-bath sweeps per step with edge-density samples every 100 sweeps
+after a 5 x 10^4 burn-in, then the height function, the north/south/east/
+west densities and the state hash.
+
+Metric: flip attempts per second (whole job, all ranks), with the dominant
+kernel's achieved fraction of the HBM roofline.  One process per GPU; for
+N > 1 (torchrun) every rank runs an independent replica of the workload
+(weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain single-threaded reference
+sampler) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ORDER = 2048
+SEED = 7
+SWEEPS = 100_000
+STRIDE = 100
+BURN = 50_000
+UNIFORM_T = 1 << 31
+WORKLOAD = "aztec_diamond_n2048_uniform_domino"
+METRIC = "flip attempts/s"
+ORACLE_SAMPLE_SWEEPS = 4     # per reference-arm step (bounded CPU sample)
+BASELINE_SAMPLE_SWEEPS = 40  # cpu_baseline sample: about 10-30 s of CPU work
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(sweeps: int):
+    import oracle as O
+    st = O.aztec(N_ORDER)
+    sites = N_ORDER * N_ORDER + (N_ORDER - 1) ** 2
+    t0 = time.perf_counter()
+    O.sweeps(O.DOMINO, st, seed=SEED, stream=0, sweep0=0, k=sweeps, t_scalar=UNIFORM_T)
+    dt = time.perf_counter() - t0
+    return sites * sweeps / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_rate(1)
+    rates, total = [], 0.0
+    for _ in range(args.steps):
+        r, dt = oracle_rate(ORACLE_SAMPLE_SWEEPS)
+        rates.append(r)
+        total += dt
+    value = args.steps * ORACLE_SAMPLE_SWEEPS * (N_ORDER * N_ORDER + (N_ORDER - 1) ** 2) / total
+    sample = "%d sweeps per step of the %s workload (of %d)" % (ORACLE_SAMPLE_SWEEPS, WORKLOAD, SWEEPS)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_ORDER, "sweeps_per_step": ORACLE_SAMPLE_SWEEPS,
+                       "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_1804_07250_gb300 as T
+
+    ctx = T.Context(local)
+    dom = T.Domain.aztec(N_ORDER)
+    info = dom.info
+    stream = torch.cuda.Stream()
+    chain = T.Chain(ctx, dom, seed=SEED, stream_id=0, th=T.thresholds(scalar=UNIFORM_T))
+    if args.kernel or args.spl:
+        chain.set_plan(args.kernel, args.spl)
+    H, W = info.height, info.width
+    height_dev = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    nsew_dev = torch.empty((4, H - 1, W - 1), dtype=torch.float64, device="cuda")
+    hash_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step(s):
+        chain.reset(stream=s)
+        chain.density_begin(STRIDE, BURN)
+        chain.run(SWEEPS, stream=s)
+        chain.read_height(height_dev, stream=s)
+        chain.read_nsew(nsew_dev, stream=s)
+        chain.state_hash(out=hash_dev, stream=s)
+
+    for _ in range(args.warmup):
+        step(stream)
+    stream.synchronize()
+    ref_hash = int(hash_dev.cpu().numpy().view(np.uint64)[0])
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = chain.launches
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total_ms += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    launches = chain.launches - launches0
+    got_hash = int(hash_dev.cpu().numpy().view(np.uint64)[0])
+    assert got_hash == ref_hash, "steps are not deterministic"
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    attempts_step = info.sites * SWEEPS
+    value = world * attempts_step * args.steps / (total_ms / 1e3)
+
+    # dominant kernel: the sweep kernel, timed alone on the same stream
+    chain.reset(stream=stream)
+    chain.run(1000, stream=stream)
+    stream.synchronize()
+    k_sweeps = 2000
+    l0 = chain.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    chain.run(k_sweeps, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    k_launches = chain.launches - l0
+    k_ms = e0.elapsed_time(e1) / k_launches
+    bytes_per_sweep = 2 * info.edges / 8
+    alg_bytes_launch = bytes_per_sweep * k_sweeps / k_launches
+    peak, peak_kind = peaks()
+    achieved = alg_bytes_launch / (k_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(WORKLOAD)
+    except Exception:
+        pass
+
+    # end to end through the C-ABI with host buffers
+    init_host = dom.initial_state()
+    h_out = np.empty((H, W), dtype=np.int32)
+    s_out = np.empty(dom.canon_shape, dtype=np.uint8)
+    n_out = np.empty((4, H - 1, W - 1), dtype=np.float64)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        chain.reset(stream=stream)
+        chain.write_state(init_host, stream=stream)       # host -> device
+        chain.density_begin(STRIDE, BURN)
+        chain.run(SWEEPS, stream=stream)
+        chain.read_state(s_out, stream=stream)            # device -> host
+        chain.read_height(h_out, stream=stream)
+        chain.read_nsew(n_out, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * attempts_step * e2e_steps / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        r, dt = oracle_rate(BASELINE_SAMPLE_SWEEPS)
+        cpu = {"value": r, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+               "sample": "%d sweeps of the %s workload from the all-horizontal start (%.1f s)"
+                         % (BASELINE_SAMPLE_SWEEPS, WORKLOAD, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N_ORDER, "sites": info.sites,
+                           "sweeps_per_step": SWEEPS, "density_stride": STRIDE, "burn_in": BURN,
+                           "threshold": UNIFORM_T, "seed": SEED,
+                           "l2": "flushed between steps (256 MB write); state is L2-sized",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": traffic, "kernel_ms": k_ms,
+                             "alg_bytes_per_launch": alg_bytes_launch},
+                "clocks": clocks,
+                "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": "attempts/s",
+                        "h2d_bytes_per_step": int(init_host.nbytes),
+                        "d2h_bytes_per_step": int(s_out.nbytes + h_out.nbytes + n_out.nbytes)},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-pass, 2 resident")
+    ap.add_argument("--spl", type=int, default=0, help="sweeps per launch (0 auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

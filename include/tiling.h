@@ -1,0 +1,287 @@
+/*
+ * tiling.h -- C-ABI of the GB300 sampler for random tilings by
+ * colour-class-parallel heat-bath Glauber dynamics (Keating & Sridhar,
+ * "Random Tilings with the GPU").
+ *
+ * The calls follow the paper's statement of the problem: a simply-connected
+ * lattice domain (Sec. 1.1), an initial tiling (Sec. 1.1, Thurston), a random
+ * walk of k sweeps driven by a seed (Sec. 2.2, host function RandomWalk) at
+ * given edge / volume / vertex weights (Sec. 1.1.1, Sec. 1.2.1, Sec. 1.2.4),
+ * and reading back the tiling, its height function (Sec. 1.1, Fig. 2; Fig. 6)
+ * and observables.
+ *
+ * Conventions
+ *  - Every call returns an int status: TL_OK (0) or a TL_E* code; nothing is
+ *    thrown across the boundary.  tl_last_error() gives a thread-local
+ *    message for the last failure on the calling thread.
+ *  - The library owns the device memory of contexts, chains and batches and
+ *    frees it in the matching *_destroy call.  Callers own every buffer they
+ *    pass in.  A pointer argument documented as "host or device" may point to
+ *    either; device pointers must belong to the context's GPU.
+ *  - `stream` arguments are a cudaStream_t (NULL = legacy default stream).
+ *    Calls that take a stream only enqueue work unless a host buffer is
+ *    involved, in which case they synchronise that stream before returning.
+ *  - A chain is not thread-safe; distinct chains may be driven from distinct
+ *    threads.  Domains are immutable after creation and may be shared.
+ *  - There is no CPU fallback: without a usable GPU every call that needs one
+ *    returns TL_ECUDA.
+ *
+ * Canonical state (the interchange layout used by tl_read_state and
+ * tl_chain_create): one uint8 (0 or 1) per lattice edge, [plane][y][x] over
+ * the domain's vertex box of width W and height H (tl_domain_get_info).
+ *  - Domino (Sec. 1.1, Sec. 2.2): plane 0 = edge (x,y)-(x+1,y), plane 1 =
+ *    edge (x,y)-(x,y+1); 1 = a domino crosses the edge.  This stores each of
+ *    the paper's redundant 4-bit tilestate bits once.
+ *  - Lozenge (Sec. 1.2.1): axial triangular lattice, neighbours +-(1,0),
+ *    +-(0,1), +-(1,1); planes 0,1,2 = edges to (x+1,y), (x,y+1), (x+1,y+1);
+ *    1 = the edge is the short diagonal of a lozenge.
+ *  - Six-vertex (Sec. 1.2.4): W = H = N+2 with the N x N model vertices at
+ *    1..N; plane 0 = edge east of (X,Y), plane 1 = edge north of (X,Y);
+ *    1 = occupied.  External half-edges are plane 0 at X = 0 and X = N and
+ *    plane 1 at Y = 0 and Y = N.
+ *
+ * Randomness: a flippable site goes UP iff u < t, where t is its heat-bath
+ * threshold and u a 32-bit uniform whose bit (31-k) is bit (rank & 31) of
+ * output word ((rank >> 5) & 3) of Philox4x32-10 (Salmon et al., SC'11)
+ * with key (seed & 0xffffffff, seed >> 32) and counter
+ * (rank >> 7, sweep, (k << 16) | pass, stream_id).  rank = r * Rp + j where
+ * (r, j) = (y, x >> 1) for dominoes, (y, x / 3) for lozenges and
+ * (Y >> 1, X >> 1) for six-vertex faces, and Rp is the number of j values
+ * per row rounded up to a multiple of 128.  `sweep` is the absolute sweep
+ * index since chain creation.  Results therefore do not depend on launch
+ * shape, batching or serving.  UP means: two vertical dominoes (tilestate
+ * 12, Sec. 2.2), a cube added (Sec. 1.2.1), or the six-vertex face path
+ * through its bottom and left edges (Fig. 5C).
+ *
+ * Passes: a sweep visits the colour classes in a fixed order -- dominoes
+ * (x+y) mod 2 = 0, 1 (Sec. 1.1.3); lozenges (x+y) mod 3 = 0, 1, 2 (Sec.
+ * 1.2.1); six-vertex faces by (X mod 2, Y mod 2) = (0,0), (1,1), (1,0),
+ * (0,1) (Sec. 1.2.4).  All sites of a class move at once (Eq. 1.1).
+ */
+#ifndef TILING_H
+#define TILING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TL_OK = 0,
+    TL_EINVAL = 1,        /* bad argument, size or state */
+    TL_ENOTSIMPLY = 2,    /* domain boundary is not a simple closed path */
+    TL_ENOTTILEABLE = 3,  /* domain has no tiling */
+    TL_ENOMEM = 4,        /* host or device allocation failed */
+    TL_EBUDGET = 5,       /* request exceeds a memory budget */
+    TL_ECUDA = 6,         /* CUDA runtime error (message has details) */
+    TL_ETIMEOUT = 7,      /* a bounded device-side wait gave up */
+    TL_EBUSY = 8,         /* resource in use */
+    TL_EUNSUPPORTED = 9   /* valid request the library does not implement */
+};
+
+typedef enum { TL_DOMINO = 0, TL_LOZENGE = 1, TL_SIXV = 2 } tl_lattice;
+
+typedef struct tl_ctx tl_ctx;
+typedef struct tl_domain tl_domain;
+typedef struct tl_chain tl_chain;
+
+/* Thread-local message describing the last failing call on this thread. */
+const char* tl_last_error(void);
+
+/* Library version string. */
+const char* tl_version(void);
+
+/* ------------------------------------------------------------------------
+ * Context: one per GPU.  cuda_device is the CUDA ordinal.  The context
+ * records the device's SM count and shared-memory limits used by the
+ * launch planner.  Errors: TL_EINVAL (bad ordinal), TL_ECUDA.
+ * ---------------------------------------------------------------------- */
+int tl_ctx_create(int cuda_device, tl_ctx** out);
+void tl_ctx_destroy(tl_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Domains (Sec. 1.1: a simply-connected union of lattice faces; Sec. 1.2.1
+ * lozenge hexagon; Sec. 1.2.4 six-vertex box with fixed boundary).
+ *  tl_domain_aztec:   Aztec diamond of order n >= 1 (faces with centres
+ *                     |cx-n| + |cy-n| <= n), box (2n+1)^2, start: every row
+ *                     of faces tiled by horizontal dominoes.
+ *  tl_domain_rect:    w x h faces, box (w+1) x (h+1); start all-horizontal
+ *                     (w even) or all-vertical (h even); TL_ENOTTILEABLE if
+ *                     w*h is odd.
+ *  tl_domain_hexagon: hexagon with sides a, b, c (an a x b x c box of cubes
+ *                     seen along (1,1,1)); box (a+c+1) x (b+c+1); start: the
+ *                     empty box (minimal height).
+ *  tl_domain_dwbc:    six-vertex N x N with domain-wall boundary (all bottom
+ *                     and left external edges occupied, top and right empty);
+ *                     start: the identity permutation (path k enters column k
+ *                     and turns left at row k).
+ * Sizes: every box side must be <= 65536 and the box <= 2^31 vertices;
+ * otherwise TL_EINVAL.  Domains live on the host and are freed with
+ * tl_domain_destroy.
+ * ---------------------------------------------------------------------- */
+int tl_domain_aztec(int n, tl_domain** out);
+int tl_domain_rect(int w, int h, tl_domain** out);
+int tl_domain_hexagon(int a, int b, int c, tl_domain** out);
+int tl_domain_dwbc(int N, tl_domain** out);
+void tl_domain_destroy(tl_domain* d);
+
+typedef struct {
+    int lattice;            /* tl_lattice */
+    int width, height;      /* vertex box W x H */
+    int planes;             /* canonical planes: 2 or 3 */
+    int passes;             /* colour classes per sweep: 2, 3 or 4 */
+    uint64_t sites;         /* flip attempts per sweep (interior sites) */
+    uint64_t edges;         /* non-redundant state bits (dual edges for
+                               dominoes/lozenges, lattice edges for 6V) */
+    uint64_t canon_bytes;   /* planes * W * H */
+    uint64_t packed_bytes;  /* device bytes of one chain's packed state */
+    uint64_t site_box;      /* W * H: entries of a per-site threshold array */
+    uint64_t height_count;  /* entries of tl_read_height output */
+    int height_width;       /* height grid width (W, or N+1 for 6V) */
+    int height_height;
+} tl_domain_info;
+
+int tl_domain_get_info(const tl_domain* d, tl_domain_info* out);
+
+/* Copy the domain's canonical starting tiling into `canon` (host, cap >=
+ * canon_bytes). */
+int tl_domain_initial_state(const tl_domain* d, uint8_t* canon, size_t cap);
+
+/* ------------------------------------------------------------------------
+ * Heat-bath thresholds, computed once on the host in FP64.  In each case
+ * t = floor(P(UP) * 2^32), clamped to [0, 2^32 - 1], with P(UP) evaluated
+ * exactly in the order written below.
+ *
+ * Domino edge weights (Sec. 1.1.1): `w` is laid out like the canonical
+ * state ([2][H][W] doubles, weight of the dual edge crossing each primal
+ * edge; n_w = 2*W*H).  For each vertex (x,y): up = wE*wW, down = wN*wS with
+ * wE = w[0][y][x], wW = w[0][y][x-1], wN = w[1][y][x], wS = w[1][y-1][x]
+ * (1.0 outside the box), P = up / (up + down).  Output t[y][x] for every box
+ * vertex (n_t = W*H).  Errors: TL_EINVAL on size mismatch, non-positive or
+ * non-finite weights.
+ * ---------------------------------------------------------------------- */
+int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w, size_t n_w,
+                                      uint32_t* t, size_t n_t);
+
+/* Lozenge q^volume (Sec. 1.1.1 volume weights on the cube picture, Sec.
+ * 1.2.1): P(add a cube) = q / (1 + q); t_add as above, t_rem = 2^32 - t_add.
+ * A flippable site ends with the cube present iff u < t_add.  TL_EINVAL if q
+ * is not positive and finite or t_add would be 0. */
+int tl_thresholds_lozenge_q(double q, uint32_t* t_add, uint32_t* t_rem);
+
+/* Six-vertex vertex weights (Sec. 1.2.4, Fig. 5A) w6 = (a1, a2, b1, b2, c1,
+ * c2).  t16[idx] for the face flip (Fig. 5C) given the four external corner
+ * bits idx = Vt(X,Y+1) | Hz(X+1,Y+1) << 1 | Hz(X+1,Y) << 2 | Hz(X-1,Y) << 3:
+ * W_A and W_B are the products of the four corner-vertex weights in the order
+ * top-left, top-right, bottom-right, bottom-left for the face's two states
+ * (A = path through right and top edges, B = through bottom and left = UP),
+ * and P = W_B / (W_A + W_B). */
+int tl_thresholds_6v(const double w6[6], uint32_t t16[16]);
+
+/* ------------------------------------------------------------------------
+ * Chains.
+ * ---------------------------------------------------------------------- */
+typedef enum {
+    TL_T_SCALAR = 0,   /* one threshold for every site (domino, lozenge) */
+    TL_T_SITE = 1,     /* per-site thresholds (domino, lozenge) */
+    TL_T_TABLE16 = 2   /* six-vertex 16-entry table */
+} tl_threshold_kind;
+
+typedef struct {
+    int kind;                 /* tl_threshold_kind */
+    uint32_t scalar;          /* TL_T_SCALAR */
+    const uint32_t* site;     /* TL_T_SITE: host array [H][W] (t per vertex) */
+    uint32_t table16[16];     /* TL_T_TABLE16 */
+} tl_thresholds;
+
+/* Create a chain on `ctx` for domain `d`.  `canon_init` (host, canon_bytes)
+ * is the starting tiling, or NULL for the domain's default start; it is
+ * checked (every face / triangle covered once, or the ice rule and the
+ * boundary for six-vertex) and TL_EINVAL is returned if it is not a valid
+ * configuration of the domain.  `seed` keys the Philox generator,
+ * `stream_id` separates independent chains.  The thresholds are copied.
+ * The chain's sweep counter starts at 0.  Errors: TL_EINVAL, TL_ENOMEM,
+ * TL_ECUDA. */
+int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon_init,
+                    uint64_t seed, uint32_t stream_id, const tl_thresholds* th,
+                    tl_chain** out);
+void tl_chain_destroy(tl_chain* c);
+
+/* Restore the chain to its creation state on `stream`: the starting
+ * configuration (from a device-side copy taken at creation), sweep counter
+ * 0, density sampling off.  Enqueues only. */
+int tl_chain_reset(tl_chain* c, void* stream);
+
+/* Absolute sweep index of the chain (number of sweeps run so far). */
+uint64_t tl_chain_sweep(const tl_chain* c);
+
+/* Run k sweeps (the loop of RandomWalk, Sec. 2.2, with a fixed pass order)
+ * on `stream`.  Enqueues only.  Density samples due inside the range (see
+ * tl_density_begin) are taken at the right sweeps.  Errors: TL_EINVAL,
+ * TL_ECUDA, TL_ETIMEOUT (a bounded device wait gave up; the chain's state is
+ * then undefined). */
+int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream);
+
+/* Run k sweeps one at a time and write the state hash after every sweep
+ * into ring[0..k-1] (uint64, host or device).  Slower; for verification. */
+int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream);
+
+/* Canonical state of the chain into `canon` (host or device, cap >=
+ * canon_bytes). */
+int tl_read_state(tl_chain* c, uint8_t* canon, size_t cap, void* stream);
+
+/* Replace the chain's state (host or device canonical buffer, n ==
+ * canon_bytes).  The configuration is validated as in tl_chain_create. */
+int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* stream);
+
+/* Order-independent state hash: sum mod 2^64 over set canonical bits i of
+ * splitmix64(i) (Steele, Lea & Flood 2014; mix of x + 0x9e3779b97f4a7c15).
+ * `out` is host or device. */
+int tl_state_hash(tl_chain* c, uint64_t* out, void* stream);
+
+/* Height function (Sec. 1.1 and Fig. 2 for dominoes: +-1 along uncrossed
+ * edges with a black face on the left counting +1, -+3 across dominoes;
+ * lozenges: the k-coordinate of the cube surface, raised by one per added
+ * cube; six-vertex Fig. 6: face heights, +1 across occupied and -1 across
+ * empty edges stepping up or right).  h = 0 at the first domain vertex in
+ * (y, x) order (six-vertex: the bottom-left outer face).  Output int32
+ * [height_height][height_width] (host or device); vertices off the domain
+ * get INT32_MIN. */
+int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream);
+
+/* Edge-occupancy sampling (the densities of Sec. 4's figures).  After this
+ * call every sweep s with s >= burn_in and (s - burn_in) % stride == 0
+ * that a later tl_run_sweeps completes (s counted after the sweep, 1-based)
+ * adds the state to per-edge uint32 counters.  Resets the counters. */
+int tl_density_begin(tl_chain* c, uint32_t stride, uint64_t burn_in);
+
+/* Per-edge density = count / samples in FP64, canonical layout
+ * [planes][H][W] (host or device doubles, cap >= canon_bytes entries).
+ * *samples (host, may be NULL) receives the number of samples. */
+int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* samples, void* stream);
+
+/* Domino only: per-face densities of the four domino types, [4][H-1][W-1]
+ * doubles (host or device) in the order north, south, east, west.  A
+ * horizontal domino is north iff its left square has the colour (x+y) mod 2
+ * == kappa; a vertical one is west iff its bottom square has colour
+ * (x+y) mod 2 != kappa; kappa = n mod 2 for the Aztec diamond of order n
+ * (so the all-horizontal start is north in the upper half) and 0 otherwise. */
+int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream);
+
+/* Launch-planner controls (for tests and tuning): sweeps per launch of the
+ * resident kernel (0 = automatic) and the kernel family: 0 automatic, 1 the
+ * one-launch-per-pass global-memory kernel, 2 the shared-memory resident
+ * multi-sweep kernel.  Results do not depend on either. */
+int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch);
+
+/* Count of kernel launches the library made on this chain since creation
+ * (all kinds).  For accounting in benchmarks. */
+uint64_t tl_chain_launches(const tl_chain* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TILING_H */

@@ -1,0 +1,336 @@
+"""GB300 sampler for random tilings by colour-class-parallel heat-bath
+Glauber dynamics (Keating & Sridhar, "Random Tilings with the GPU").
+
+Thin ctypes binding over ``libtiling.so`` (the C-ABI in ``include/tiling.h``):
+argument marshalling only.  Every step of the sampler runs in the library's
+CUDA kernels; there is no CPU fallback, and importing this package fails if
+the library has not been built (``paper_1804_07250_gb300._build.build()``).
+
+Buffers may be numpy arrays (host) or torch tensors (host or CUDA); streams
+may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer or None (the
+legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtiling.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libtiling.so is missing: build it with "
+                      "`python -m paper_1804_07250_gb300._build` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+TL_OK, TL_EINVAL, TL_ENOTSIMPLY, TL_ENOTTILEABLE, TL_ENOMEM = 0, 1, 2, 3, 4
+TL_EBUDGET, TL_ECUDA, TL_ETIMEOUT, TL_EBUSY, TL_EUNSUPPORTED = 5, 6, 7, 8, 9
+DOMINO, LOZENGE, SIXV = 0, 1, 2
+T_SCALAR, T_SITE, T_TABLE16 = 0, 1, 2
+
+_ERRNAMES = {1: "EINVAL", 2: "ENOTSIMPLY", 3: "ENOTTILEABLE", 4: "ENOMEM", 5: "EBUDGET",
+             6: "ECUDA", 7: "ETIMEOUT", 8: "EBUSY", 9: "EUNSUPPORTED"}
+
+
+class TilingError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_ERRNAMES.get(code, code), msg))
+        self.code = code
+
+
+class DomainInfo(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("planes", ctypes.c_int), ("passes", ctypes.c_int), ("sites", ctypes.c_uint64),
+                ("edges", ctypes.c_uint64), ("canon_bytes", ctypes.c_uint64),
+                ("packed_bytes", ctypes.c_uint64), ("site_box", ctypes.c_uint64),
+                ("height_count", ctypes.c_uint64), ("height_width", ctypes.c_int),
+                ("height_height", ctypes.c_int)]
+
+
+class Thresholds(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("scalar", ctypes.c_uint32),
+                ("site", ctypes.c_void_p), ("table16", ctypes.c_uint32 * 16)]
+
+
+_vp, _u64, _u32, _i = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_SIG = {
+    "tl_last_error": (ctypes.c_char_p, []),
+    "tl_version": (ctypes.c_char_p, []),
+    "tl_ctx_create": (_i, [_i, ctypes.POINTER(_vp)]),
+    "tl_ctx_destroy": (None, [_vp]),
+    "tl_domain_aztec": (_i, [_i, ctypes.POINTER(_vp)]),
+    "tl_domain_rect": (_i, [_i, _i, ctypes.POINTER(_vp)]),
+    "tl_domain_hexagon": (_i, [_i, _i, _i, ctypes.POINTER(_vp)]),
+    "tl_domain_dwbc": (_i, [_i, ctypes.POINTER(_vp)]),
+    "tl_domain_destroy": (None, [_vp]),
+    "tl_domain_get_info": (_i, [_vp, ctypes.POINTER(DomainInfo)]),
+    "tl_domain_initial_state": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "tl_thresholds_domino_edge_weights": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]),
+    "tl_thresholds_lozenge_q": (_i, [ctypes.c_double, _vp, _vp]),
+    "tl_thresholds_6v": (_i, [_vp, _vp]),
+    "tl_chain_create": (_i, [_vp, _vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds),
+                             ctypes.POINTER(_vp)]),
+    "tl_chain_destroy": (None, [_vp]),
+    "tl_chain_reset": (_i, [_vp, _vp]),
+    "tl_chain_sweep": (_u64, [_vp]),
+    "tl_chain_launches": (_u64, [_vp]),
+    "tl_chain_set_plan": (_i, [_vp, _i, _i]),
+    "tl_run_sweeps": (_i, [_vp, _u64, _vp]),
+    "tl_run_sweeps_hashed": (_i, [_vp, _u64, _vp, _vp]),
+    "tl_read_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "tl_write_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "tl_state_hash": (_i, [_vp, _vp, _vp]),
+    "tl_read_height": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "tl_density_begin": (_i, [_vp, _u32, _u64]),
+    "tl_read_density": (_i, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
+    "tl_read_domino_nsew": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+}
+for _name, (_res, _args) in _SIG.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIG)
+
+
+def lib():
+    return _lib
+
+
+def _check(rc):
+    if rc != TL_OK:
+        raise TilingError(rc, _lib.tl_last_error().decode(errors="replace"))
+
+
+def version() -> str:
+    return _lib.tl_version().decode()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(getattr(s, "cuda_stream"))
+
+
+def _ptr(buf):
+    """Data pointer and byte size of a numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"], "buffer must be contiguous"
+        return buf.ctypes.data, buf.nbytes
+    if hasattr(buf, "data_ptr"):
+        assert buf.is_contiguous(), "buffer must be contiguous"
+        return buf.data_ptr(), buf.numel() * buf.element_size()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(_lib.tl_ctx_create(device, ctypes.byref(h)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _lib.tl_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Domain:
+    def __init__(self, handle):
+        self._h = handle
+        info = DomainInfo()
+        _check(_lib.tl_domain_get_info(self._h, ctypes.byref(info)))
+        self.info = info
+
+    @classmethod
+    def aztec(cls, n):
+        h = _vp(); _check(_lib.tl_domain_aztec(n, ctypes.byref(h))); return cls(h)
+
+    @classmethod
+    def rect(cls, w, h_):
+        h = _vp(); _check(_lib.tl_domain_rect(w, h_, ctypes.byref(h))); return cls(h)
+
+    @classmethod
+    def hexagon(cls, a, b, c):
+        h = _vp(); _check(_lib.tl_domain_hexagon(a, b, c, ctypes.byref(h))); return cls(h)
+
+    @classmethod
+    def dwbc(cls, N):
+        h = _vp(); _check(_lib.tl_domain_dwbc(N, ctypes.byref(h))); return cls(h)
+
+    @property
+    def canon_shape(self):
+        return (self.info.planes, self.info.height, self.info.width)
+
+    @property
+    def height_shape(self):
+        return (self.info.height_height, self.info.height_width)
+
+    def initial_state(self) -> np.ndarray:
+        out = np.zeros(self.canon_shape, dtype=np.uint8)
+        p, n = _ptr(out)
+        _check(_lib.tl_domain_initial_state(self._h, p, n))
+        return out
+
+    def domino_thresholds(self, w: np.ndarray) -> np.ndarray:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        t = np.zeros((self.info.height, self.info.width), dtype=np.uint32)
+        pw, _ = _ptr(w)
+        pt, _ = _ptr(t)
+        _check(_lib.tl_thresholds_domino_edge_weights(self._h, pw, w.size, pt, t.size))
+        return t
+
+    def close(self):
+        if self._h:
+            _lib.tl_domain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lozenge_thresholds(q: float):
+    a = np.zeros(1, dtype=np.uint32)
+    r = np.zeros(1, dtype=np.uint32)
+    _check(_lib.tl_thresholds_lozenge_q(q, a.ctypes.data, r.ctypes.data))
+    return int(a[0]), int(r[0])
+
+
+def sixv_thresholds(w6) -> np.ndarray:
+    w = np.ascontiguousarray(w6, dtype=np.float64)
+    t = np.zeros(16, dtype=np.uint32)
+    _check(_lib.tl_thresholds_6v(w.ctypes.data, t.ctypes.data))
+    return t
+
+
+def thresholds(scalar=None, site=None, table16=None) -> Thresholds:
+    th = Thresholds()
+    if table16 is not None:
+        th.kind = T_TABLE16
+        for i, v in enumerate(np.asarray(table16, dtype=np.uint32)):
+            th.table16[i] = int(v)
+    elif site is not None:
+        th.kind = T_SITE
+        th._site = np.ascontiguousarray(site, dtype=np.uint32)
+        th.site = th._site.ctypes.data
+    else:
+        th.kind = T_SCALAR
+        th.scalar = int(scalar if scalar is not None else 1 << 31)
+    return th
+
+
+class Chain:
+    """One Markov chain resident on the GPU."""
+
+    def __init__(self, ctx: Context, domain: Domain, *, seed: int, stream_id: int = 0,
+                 th: Thresholds | None = None, init: np.ndarray | None = None):
+        self.ctx, self.domain = ctx, domain
+        self._th = th if th is not None else thresholds()
+        p = None
+        if init is not None:
+            init = np.ascontiguousarray(init, dtype=np.uint8)
+            assert init.shape == domain.canon_shape
+            p = init.ctypes.data
+        h = _vp()
+        _check(_lib.tl_chain_create(ctx._h, domain._h, p, seed, stream_id,
+                                    ctypes.byref(self._th), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def sweep(self) -> int:
+        return int(_lib.tl_chain_sweep(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.tl_chain_launches(self._h))
+
+    def reset(self, stream=None):
+        _check(_lib.tl_chain_reset(self._h, _stream(stream)))
+
+    def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0):
+        _check(_lib.tl_chain_set_plan(self._h, kernel, sweeps_per_launch))
+
+    def run(self, k: int, stream=None):
+        _check(_lib.tl_run_sweeps(self._h, k, _stream(stream)))
+
+    def run_hashed(self, k: int, ring=None, stream=None):
+        if ring is None:
+            ring = np.zeros(k, dtype=np.uint64)
+        p, n = _ptr(ring)
+        assert n >= 8 * k
+        _check(_lib.tl_run_sweeps_hashed(self._h, k, p, _stream(stream)))
+        return ring
+
+    def read_state(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.domain.canon_shape, dtype=np.uint8)
+        p, n = _ptr(out)
+        _check(_lib.tl_read_state(self._h, p, n, _stream(stream)))
+        return out
+
+    def write_state(self, state, stream=None):
+        if isinstance(state, np.ndarray):
+            state = np.ascontiguousarray(state, dtype=np.uint8)
+        p, n = _ptr(state)
+        _check(_lib.tl_write_state(self._h, p, n, _stream(stream)))
+
+    def state_hash(self, out=None, stream=None) -> int:
+        if out is not None:
+            p, _ = _ptr(out)
+            _check(_lib.tl_state_hash(self._h, p, _stream(stream)))
+            return None
+        v = np.zeros(1, dtype=np.uint64)
+        _check(_lib.tl_state_hash(self._h, v.ctypes.data, _stream(stream)))
+        return int(v[0])
+
+    def read_height(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.domain.height_shape, dtype=np.int32)
+        p, n = _ptr(out)
+        _check(_lib.tl_read_height(self._h, p, n // 4, _stream(stream)))
+        return out
+
+    def density_begin(self, stride: int, burn_in: int = 0):
+        _check(_lib.tl_density_begin(self._h, stride, burn_in))
+
+    def read_density(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.domain.canon_shape, dtype=np.float64)
+        p, n = _ptr(out)
+        s = np.zeros(1, dtype=np.uint64)
+        _check(_lib.tl_read_density(self._h, p, n // 8, s.ctypes.data, _stream(stream)))
+        return out, int(s[0])
+
+    def read_nsew(self, out=None, stream=None):
+        H, W = self.domain.info.height, self.domain.info.width
+        if out is None:
+            out = np.zeros((4, H - 1, W - 1), dtype=np.float64)
+        p, n = _ptr(out)
+        _check(_lib.tl_read_domino_nsew(self._h, p, n // 8, _stream(stream)))
+        return out
+
+    def close(self):
+        if self._h:
+            _lib.tl_chain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

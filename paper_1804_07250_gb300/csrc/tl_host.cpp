@@ -1,0 +1,993 @@
+// Host runtime of the C-ABI in include/tiling.h: domain builders, FP64
+// heat-bath thresholds, chain state management and the launch planner.
+#include "tiling.h"
+#include "tl_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace tl;
+
+#define TL_API extern "C" __attribute__((visibility("default")))
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (cudaError_t)(expr);                                           \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(TL_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));     \
+    } while (0)
+
+TL_API const char* tl_last_error(void) { return g_err.c_str(); }
+TL_API const char* tl_version(void) { return "tiling-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct tl_ctx {
+    int device;
+    int sms;
+    int smem_optin;
+    int l2_bytes;
+};
+
+TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
+{
+    if (!out) return fail(TL_EINVAL, "tl_ctx_create: out is NULL");
+    int n = 0;
+    CUDA_TRY(cudaGetDeviceCount(&n));
+    if (cuda_device < 0 || cuda_device >= n)
+        return fail(TL_EINVAL, "tl_ctx_create: device %d of %d", cuda_device, n);
+    CUDA_TRY(cudaSetDevice(cuda_device));
+    tl_ctx* c = new (std::nothrow) tl_ctx();
+    if (!c) return fail(TL_ENOMEM, "tl_ctx_create: host allocation");
+    c->device = cuda_device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, cuda_device);
+    cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cuda_device);
+    cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, cuda_device);
+    *out = c;
+    return TL_OK;
+}
+
+TL_API void tl_ctx_destroy(tl_ctx* c) { delete c; }
+
+// ---------------------------------------------------------------------------
+// Domains
+// ---------------------------------------------------------------------------
+struct tl_domain {
+    Geom g;
+    std::vector<uint8_t> init;        // canonical starting configuration
+    std::vector<uint8_t> cover;       // domino: faces [H-1][W-1]; lozenge: up/down [2][H][W]
+    uint64_t sites = 0, edges = 0;
+    std::vector<int2> grange;         // per site row: [first, last+1) active groups
+    int hw = 0, hh = 0;
+    std::vector<int> hxlo, hxhi, hspine;
+    int kappa = 0;
+};
+
+static Geom make_geom(int lattice, int W, int H, int N)
+{
+    Geom g{};
+    g.lattice = lattice;
+    g.W = W;
+    g.H = H;
+    g.N = N;
+    g.npar = (lattice == LAT_LOZENGE) ? 3 : 2;
+    g.ntype = (lattice == LAT_LOZENGE) ? 3 : 2;
+    g.P = g.npar * g.ntype;
+    const int64_t wj = (W + g.npar - 1) / g.npar;
+    const int64_t rp = (wj + 127) / 128 * 128;
+    g.K = (int)(rp / 32);
+    g.Kg = g.K / 4;
+    g.passes = (lattice == LAT_DOMINO) ? 2 : (lattice == LAT_LOZENGE ? 3 : 4);
+    g.row_words = (int64_t)g.P * g.K;
+    g.total_words = (int64_t)(H + 2) * g.row_words;
+    return g;
+}
+
+static bool box_ok(int64_t W, int64_t H)
+{
+    return W >= 2 && H >= 2 && W <= 65536 && H <= 65536 && W * H <= (int64_t)1 << 31;
+}
+
+// Edge access on a canonical array, zero outside the box.
+struct Canon {
+    const uint8_t* s;
+    int W, H;
+    int at(int type, int x, int y) const
+    {
+        if (x < 0 || y < 0 || x >= W || y >= H) return 0;
+        return s[((size_t)type * H + y) * W + x];
+    }
+};
+
+static void set_group_range(tl_domain* d, int row, int jmin, int jmax)
+{
+    if (jmin > jmax) d->grange[row] = make_int2(0, 0);
+    else d->grange[row] = make_int2(jmin >> 7, (jmax >> 7) + 1);
+}
+
+// Height rows over a grid of hw x hh points given a membership test for
+// points and for the horizontal / vertical unit steps between them.
+template <class InV, class InH, class InVert>
+static int plan_heights(tl_domain* d, int hw, int hh, InV inv, InH inh, InVert invert)
+{
+    d->hw = hw;
+    d->hh = hh;
+    d->hxlo.assign(hh, 1);
+    d->hxhi.assign(hh, 0);
+    d->hspine.assign(hh, -1);
+    int prev = -1;
+    for (int y = 0; y < hh; ++y) {
+        int lo = -1, hi = -1;
+        for (int x = 0; x < hw; ++x)
+            if (inv(x, y)) {
+                if (lo < 0) lo = x;
+                hi = x;
+            }
+        if (lo < 0) continue;
+        for (int x = lo; x < hi; ++x)
+            if (!inv(x, y) || !inh(x, y))
+                return fail(TL_EUNSUPPORTED, "height: row %d of the domain is not an interval", y);
+        d->hxlo[y] = lo;
+        d->hxhi[y] = hi;
+        if (prev >= 0) {
+            if (prev != y - 1) return fail(TL_EUNSUPPORTED, "height: domain rows are not contiguous");
+            int xs = -1;
+            for (int x = std::max(lo, d->hxlo[prev]); x <= std::min(hi, d->hxhi[prev]); ++x)
+                if (invert(x, y)) { xs = x; break; }
+            if (xs < 0) return fail(TL_EUNSUPPORTED, "height: rows %d and %d are not linked", y - 1, y);
+            d->hspine[y] = xs;
+        }
+        prev = y;
+    }
+    return TL_OK;
+}
+
+// Derive the face set, sites, group ranges and height plan of a domino
+// domain from a tiling of it.
+static int analyse_domino(tl_domain* d, int aztec_n)
+{
+    const Geom& g = d->g;
+    const int W = g.W, H = g.H;
+    Canon c{d->init.data(), W, H};
+    d->cover.assign((size_t)(W - 1) * (H - 1), 0);
+    auto face = [&](int x, int y) -> int {
+        if (x < 0 || y < 0 || x >= W - 1 || y >= H - 1) return 0;
+        return d->cover[(size_t)y * (W - 1) + x];
+    };
+    for (int y = 0; y < H - 1; ++y)
+        for (int x = 0; x < W - 1; ++x) {
+            const int k = c.at(0, x, y) + c.at(0, x, y + 1) + c.at(1, x, y) + c.at(1, x + 1, y);
+            if (k > 1) return fail(TL_EINVAL, "domino: face (%d,%d) covered twice", x, y);
+            d->cover[(size_t)y * (W - 1) + x] = (uint8_t)k;
+        }
+    d->grange.assign(H, make_int2(0, 0));
+    d->sites = 0;
+    for (int y = 0; y < H; ++y) {
+        int jmin = 1 << 30, jmax = -1;
+        for (int x = 0; x < W; ++x)
+            if (face(x - 1, y - 1) && face(x, y - 1) && face(x - 1, y) && face(x, y)) {
+                ++d->sites;
+                jmin = std::min(jmin, x >> 1);
+                jmax = std::max(jmax, x >> 1);
+            }
+        set_group_range(d, y, jmin, jmax);
+    }
+    d->edges = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            d->edges += face(x, y - 1) && face(x, y);   // horizontal edge between two faces
+            d->edges += face(x - 1, y) && face(x, y);   // vertical edge between two faces
+        }
+    d->kappa = aztec_n > 0 ? (aztec_n & 1) : 0;
+    auto inv = [&](int x, int y) { return face(x, y) || face(x - 1, y) || face(x, y - 1) || face(x - 1, y - 1); };
+    auto inh = [&](int x, int y) { return face(x, y) || face(x, y - 1); };
+    auto invert = [&](int x, int y) { return face(x - 1, y - 1) || face(x, y - 1); };
+    return plan_heights(d, W, H, inv, inh, invert);
+}
+
+static int analyse_lozenge(tl_domain* d)
+{
+    const Geom& g = d->g;
+    const int W = g.W, H = g.H;
+    Canon c{d->init.data(), W, H};
+    // triangles with lower-left corner in [-1, W) x [-1, H) stored with offset 1
+    const int TW = W + 1, TH = H + 1;
+    d->cover.assign((size_t)2 * TW * TH, 0);
+    auto tu = [&](int x, int y) -> int {
+        if (x < -1 || y < -1 || x >= W || y >= H) return 0;
+        return d->cover[(size_t)(y + 1) * TW + (x + 1)];
+    };
+    auto td = [&](int x, int y) -> int {
+        if (x < -1 || y < -1 || x >= W || y >= H) return 0;
+        return d->cover[(size_t)TW * TH + (size_t)(y + 1) * TW + (x + 1)];
+    };
+    for (int y = -1; y < H; ++y)
+        for (int x = -1; x < W; ++x) {
+            const int u = c.at(0, x, y) + c.at(1, x + 1, y) + c.at(2, x, y);
+            const int v = c.at(2, x, y) + c.at(1, x, y) + c.at(0, x, y + 1);
+            if (u > 1 || v > 1) return fail(TL_EINVAL, "lozenge: triangle at (%d,%d) covered twice", x, y);
+            d->cover[(size_t)(y + 1) * TW + (x + 1)] = (uint8_t)u;
+            d->cover[(size_t)TW * TH + (size_t)(y + 1) * TW + (x + 1)] = (uint8_t)v;
+        }
+    d->grange.assign(H, make_int2(0, 0));
+    d->sites = 0;
+    for (int y = 0; y < H; ++y) {
+        int jmin = 1 << 30, jmax = -1;
+        for (int x = 0; x < W; ++x)
+            if (tu(x, y) && td(x, y) && tu(x - 1, y) && td(x - 1, y - 1) && tu(x - 1, y - 1) && td(x, y - 1)) {
+                ++d->sites;
+                jmin = std::min(jmin, x / 3);
+                jmax = std::max(jmax, x / 3);
+            }
+        set_group_range(d, y, jmin, jmax);
+    }
+    d->edges = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            d->edges += tu(x, y) && td(x, y - 1);       // E1(x,y)
+            d->edges += td(x, y) && tu(x - 1, y);       // E2(x,y)
+            d->edges += tu(x, y) && td(x, y);           // E3(x,y)
+        }
+    auto inv = [&](int x, int y) {
+        return tu(x, y) || td(x, y) || tu(x - 1, y) || td(x - 1, y - 1) || tu(x - 1, y - 1) || td(x, y - 1);
+    };
+    auto inh = [&](int x, int y) { return tu(x, y) || td(x, y - 1); };
+    auto invert = [&](int x, int y) { return td(x, y - 1) || tu(x - 1, y - 1); };
+    return plan_heights(d, W, H, inv, inh, invert);
+}
+
+static int analyse_sixv(tl_domain* d)
+{
+    const int N = d->g.N;
+    d->grange.assign(d->g.H, make_int2(0, 0));
+    const int gmax = (((N - 1) >> 1) >> 7) + 1;
+    for (int Y = 1; Y <= N - 1; ++Y) d->grange[Y] = make_int2(0, gmax);
+    d->sites = (uint64_t)(N - 1) * (N - 1);
+    d->edges = (uint64_t)2 * N * (N - 1);
+    d->hw = d->hh = N + 1;
+    d->hxlo.assign(N + 1, 0);
+    d->hxhi.assign(N + 1, N);
+    d->hspine.assign(N + 1, 0);
+    d->hspine[0] = -1;
+    return TL_OK;
+}
+
+static int finish_domain(tl_domain* d, int aztec_n, tl_domain** out)
+{
+    int rc;
+    if (d->g.lattice == LAT_DOMINO) rc = analyse_domino(d, aztec_n);
+    else if (d->g.lattice == LAT_LOZENGE) rc = analyse_lozenge(d);
+    else rc = analyse_sixv(d);
+    if (rc != TL_OK) {
+        delete d;
+        return rc;
+    }
+    *out = d;
+    return TL_OK;
+}
+
+// Aztec diamond of order n.  Each row of faces is an interval centred on
+// x = n; the start tiles every row with horizontal dominoes from its left end.
+TL_API int tl_domain_aztec(int n, tl_domain** out)
+{
+    if (!out || n < 1 || !box_ok(2 * (int64_t)n + 1, 2 * (int64_t)n + 1))
+        return fail(TL_EINVAL, "tl_domain_aztec: bad order %d", n);
+    tl_domain* d = new (std::nothrow) tl_domain();
+    if (!d) return fail(TL_ENOMEM, "tl_domain_aztec: host allocation");
+    const int W = 2 * n + 1;
+    d->g = make_geom(LAT_DOMINO, W, W, 0);
+    d->init.assign((size_t)2 * W * W, 0);
+    uint8_t* vt = d->init.data() + (size_t)W * W;
+    for (int fy = 0; fy < 2 * n; ++fy) {
+        const int half = (fy < n) ? fy + 1 : 2 * n - fy;   // faces per half-row
+        for (int fx = n - half; fx < n + half; fx += 2) vt[(size_t)fy * W + fx + 1] = 1;
+    }
+    return finish_domain(d, n, out);
+}
+
+TL_API int tl_domain_rect(int w, int h, tl_domain** out)
+{
+    if (!out || w < 1 || h < 1 || !box_ok((int64_t)w + 1, (int64_t)h + 1))
+        return fail(TL_EINVAL, "tl_domain_rect: bad size %dx%d", w, h);
+    if ((int64_t)w * h % 2) return fail(TL_ENOTTILEABLE, "tl_domain_rect: %dx%d has odd area", w, h);
+    tl_domain* d = new (std::nothrow) tl_domain();
+    if (!d) return fail(TL_ENOMEM, "tl_domain_rect: host allocation");
+    const int W = w + 1, H = h + 1;
+    d->g = make_geom(LAT_DOMINO, W, H, 0);
+    d->init.assign((size_t)2 * W * H, 0);
+    uint8_t* hz = d->init.data();
+    uint8_t* vt = d->init.data() + (size_t)W * H;
+    for (int fy = 0; fy < h; ++fy)
+        for (int fx = 0; fx < w; ++fx) {
+            if (w % 2 == 0) {
+                if (fx % 2 == 0) vt[(size_t)fy * W + fx + 1] = 1;
+            } else if (fy % 2 == 0) {
+                hz[(size_t)(fy + 1) * W + fx] = 1;
+            }
+        }
+    return finish_domain(d, 0, out);
+}
+
+// Hexagon a x b x c: the tiling of a plane partition pi (heights of the
+// cube stacks over the a x b floor) seen along (1,1,1).  A unit square of
+// the stepped surface is a lozenge whose short diagonal is an edge of the
+// triangular lattice; a point (i,j,k) maps to the box vertex
+// (i - k + c, j - k + c).  The start is pi = 0 (the empty box).
+TL_API int tl_domain_hexagon(int a, int b, int c, tl_domain** out)
+{
+    if (!out || a < 1 || b < 1 || c < 1 || !box_ok((int64_t)a + c + 1, (int64_t)b + c + 1))
+        return fail(TL_EINVAL, "tl_domain_hexagon: bad sides %d,%d,%d", a, b, c);
+    tl_domain* d = new (std::nothrow) tl_domain();
+    if (!d) return fail(TL_ENOMEM, "tl_domain_hexagon: host allocation");
+    const int W = a + c + 1, H = b + c + 1;
+    d->g = make_geom(LAT_LOZENGE, W, H, 0);
+    d->init.assign((size_t)3 * W * H, 0);
+    auto mark = [&](int type, int i, int j, int k) {
+        // short diagonal from the corner (i,j,k) of a unit square
+        int x = i - k + c, y = j - k + c;
+        if (type == 0) x -= 1;        // square normal to e1: diagonal to (-1, 0)
+        else if (type == 1) y -= 1;   // square normal to e2: diagonal to (0, -1)
+        d->init[((size_t)type * H + y) * W + x] = 1;
+    };
+    for (int i = 0; i < a; ++i)
+        for (int j = 0; j < b; ++j) mark(2, i, j, 0);   // floor, normal e3
+    for (int j = 0; j < b; ++j)
+        for (int k = 0; k < c; ++k) mark(0, 0, j, k);   // wall x = 0, normal e1
+    for (int i = 0; i < a; ++i)
+        for (int k = 0; k < c; ++k) mark(1, i, 0, k);   // wall y = 0, normal e2
+    return finish_domain(d, 0, out);
+}
+
+// Domain-wall boundary: bottom and left external edges occupied.  Start:
+// the path entering column k+1 goes up to row k+1 and leaves to the left.
+TL_API int tl_domain_dwbc(int N, tl_domain** out)
+{
+    if (!out || N < 2 || !box_ok((int64_t)N + 2, (int64_t)N + 2))
+        return fail(TL_EINVAL, "tl_domain_dwbc: bad size %d", N);
+    tl_domain* d = new (std::nothrow) tl_domain();
+    if (!d) return fail(TL_ENOMEM, "tl_domain_dwbc: host allocation");
+    const int B = N + 2;
+    d->g = make_geom(LAT_SIXV, B, B, N);
+    d->init.assign((size_t)2 * B * B, 0);
+    uint8_t* hz = d->init.data();
+    uint8_t* vt = d->init.data() + (size_t)B * B;
+    for (int col = 1; col <= N; ++col) {
+        for (int Y = 0; Y < col; ++Y) vt[(size_t)Y * B + col] = 1;     // up column `col`
+        for (int X = 0; X < col; ++X) hz[(size_t)col * B + X] = 1;     // left along row `col`
+    }
+    return finish_domain(d, 0, out);
+}
+
+TL_API void tl_domain_destroy(tl_domain* d) { delete d; }
+
+TL_API int tl_domain_get_info(const tl_domain* d, tl_domain_info* o)
+{
+    if (!d || !o) return fail(TL_EINVAL, "tl_domain_get_info: NULL argument");
+    o->lattice = d->g.lattice;
+    o->width = d->g.W;
+    o->height = d->g.H;
+    o->planes = d->g.ntype;
+    o->passes = d->g.passes;
+    o->sites = d->sites;
+    o->edges = d->edges;
+    o->canon_bytes = (uint64_t)d->g.ntype * d->g.W * d->g.H;
+    o->packed_bytes = (uint64_t)d->g.total_words * 4;
+    o->site_box = (uint64_t)d->g.W * d->g.H;
+    o->height_count = (uint64_t)d->hw * d->hh;
+    o->height_width = d->hw;
+    o->height_height = d->hh;
+    return TL_OK;
+}
+
+TL_API int tl_domain_initial_state(const tl_domain* d, uint8_t* canon, size_t cap)
+{
+    if (!d || !canon) return fail(TL_EINVAL, "tl_domain_initial_state: NULL argument");
+    if (cap < d->init.size()) return fail(TL_EINVAL, "tl_domain_initial_state: cap %zu < %zu", cap, d->init.size());
+    std::memcpy(canon, d->init.data(), d->init.size());
+    return TL_OK;
+}
+
+// A canonical configuration is valid for the domain if it covers exactly
+// the domain's faces (triangles) once each, or for six-vertex if every model
+// vertex obeys the ice rule and the external edges match the boundary.
+static int validate(const tl_domain* d, const uint8_t* s)
+{
+    const Geom& g = d->g;
+    Canon c{s, g.W, g.H};
+    const size_t n = (size_t)g.ntype * g.W * g.H;
+    for (size_t i = 0; i < n; ++i)
+        if (s[i] > 1) return fail(TL_EINVAL, "state byte %zu is %d (must be 0 or 1)", i, s[i]);
+    if (g.lattice == LAT_DOMINO) {
+        for (int y = 0; y < g.H; ++y)
+            if (c.at(0, g.W - 1, y)) return fail(TL_EINVAL, "domino: edge outside the box set");
+        for (int x = 0; x < g.W; ++x)
+            if (c.at(1, x, g.H - 1)) return fail(TL_EINVAL, "domino: edge outside the box set");
+        for (int y = 0; y < g.H - 1; ++y)
+            for (int x = 0; x < g.W - 1; ++x) {
+                const int k = c.at(0, x, y) + c.at(0, x, y + 1) + c.at(1, x, y) + c.at(1, x + 1, y);
+                if (k != d->cover[(size_t)y * (g.W - 1) + x])
+                    return fail(TL_EINVAL, "domino: face (%d,%d) covered %d times", x, y, k);
+            }
+        return TL_OK;
+    }
+    if (g.lattice == LAT_LOZENGE) {
+        const int TW = g.W + 1, TH = g.H + 1;
+        for (int y = -1; y < g.H; ++y)
+            for (int x = -1; x < g.W; ++x) {
+                const int u = c.at(0, x, y) + c.at(1, x + 1, y) + c.at(2, x, y);
+                const int v = c.at(2, x, y) + c.at(1, x, y) + c.at(0, x, y + 1);
+                if (u != d->cover[(size_t)(y + 1) * TW + (x + 1)] ||
+                    v != d->cover[(size_t)TW * TH + (size_t)(y + 1) * TW + (x + 1)])
+                    return fail(TL_EINVAL, "lozenge: triangles at (%d,%d) not covered once", x, y);
+            }
+        return TL_OK;
+    }
+    const int N = g.N;
+    for (int Y = 0; Y < g.H; ++Y)
+        for (int X = 0; X < g.W; ++X) {
+            const bool hreal = Y >= 1 && Y <= N && X <= N;
+            const bool vreal = X >= 1 && X <= N && Y <= N;
+            if ((c.at(0, X, Y) && !hreal) || (c.at(1, X, Y) && !vreal))
+                return fail(TL_EINVAL, "six-vertex: bit set off the lattice at (%d,%d)", X, Y);
+        }
+    for (int k = 1; k <= N; ++k)
+        if (c.at(0, 0, k) != d->init[(size_t)k * g.W] || c.at(0, N, k) != d->init[(size_t)k * g.W + N] ||
+            c.at(1, k, 0) != d->init[(size_t)g.W * g.H + k] ||
+            c.at(1, k, N) != d->init[(size_t)g.W * g.H + (size_t)N * g.W + k])
+            return fail(TL_EINVAL, "six-vertex: external edges differ from the boundary");
+    for (int Y = 1; Y <= N; ++Y)
+        for (int X = 1; X <= N; ++X) {
+            const int L = c.at(0, X - 1, Y), R = c.at(0, X, Y), D = c.at(1, X, Y - 1), U = c.at(1, X, Y);
+            if (L + U != D + R) return fail(TL_EINVAL, "six-vertex: ice rule fails at (%d,%d)", X, Y);
+        }
+    return TL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thresholds (FP64 on the host)
+// ---------------------------------------------------------------------------
+static uint32_t to_threshold(double p)
+{
+    const double t = std::floor(p * 4294967296.0);
+    if (!(t > 0.0)) return 0u;
+    if (t >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)t;
+}
+
+TL_API int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w, size_t n_w,
+                                             uint32_t* t, size_t n_t)
+{
+    if (!d || !w || !t) return fail(TL_EINVAL, "domino thresholds: NULL argument");
+    if (d->g.lattice != LAT_DOMINO) return fail(TL_EINVAL, "domino thresholds: not a domino domain");
+    const int W = d->g.W, H = d->g.H;
+    if (n_w != (size_t)2 * W * H || n_t != (size_t)W * H)
+        return fail(TL_EINVAL, "domino thresholds: sizes %zu/%zu, want %zu/%zu", n_w, n_t,
+                    (size_t)2 * W * H, (size_t)W * H);
+    for (size_t i = 0; i < n_w; ++i)
+        if (!(w[i] > 0.0) || !std::isfinite(w[i])) return fail(TL_EINVAL, "domino thresholds: weight %zu not positive", i);
+    const double* hz = w;
+    const double* vt = w + (size_t)W * H;
+    auto H_ = [&](int x, int y) { return (x < 0 || y < 0 || x >= W || y >= H) ? 1.0 : hz[(size_t)y * W + x]; };
+    auto V_ = [&](int x, int y) { return (x < 0 || y < 0 || x >= W || y >= H) ? 1.0 : vt[(size_t)y * W + x]; };
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double up = H_(x, y) * H_(x - 1, y);
+            const double down = V_(x, y) * V_(x, y - 1);
+            t[(size_t)y * W + x] = to_threshold(up / (up + down));
+        }
+    return TL_OK;
+}
+
+TL_API int tl_thresholds_lozenge_q(double q, uint32_t* t_add, uint32_t* t_rem)
+{
+    if (!t_add || !t_rem || !(q > 0.0) || !std::isfinite(q)) return fail(TL_EINVAL, "lozenge thresholds: bad q");
+    const uint32_t ta = to_threshold(q / (1.0 + q));
+    if (ta == 0) return fail(TL_EINVAL, "lozenge thresholds: q=%g gives t_add = 0", q);
+    *t_add = ta;
+    *t_rem = (uint32_t)((((uint64_t)1) << 32) - ta);
+    return TL_OK;
+}
+
+// Corner vertex types of a face in its two states (Fig. 5A types
+// a1=0 a2=1 b1=2 b2=3 c1=4 c2=5), keyed by the corner's external bit.
+// Rows: top-left (bit Vt(X,Y+1)), top-right (Hz(X+1,Y+1)), bottom-right
+// (Hz(X+1,Y)), bottom-left (Hz(X-1,Y)); entries {A-type, B-type} for the
+// bit = 0 and bit = 1.
+static const int kCorner[4][2][2] = {
+    {{2, 4}, {5, 3}},   // TL: 0 -> (b1, c1), 1 -> (c2, b2)
+    {{4, 0}, {1, 5}},   // TR: 0 -> (c1, a1), 1 -> (a2, c2)
+    {{3, 4}, {5, 2}},   // BR: 0 -> (b2, c1), 1 -> (c2, b1)
+    {{0, 5}, {4, 1}},   // BL: 0 -> (a1, c2), 1 -> (c1, a2)
+};
+
+TL_API int tl_thresholds_6v(const double w6[6], uint32_t t16[16])
+{
+    if (!w6 || !t16) return fail(TL_EINVAL, "six-vertex thresholds: NULL argument");
+    for (int i = 0; i < 6; ++i)
+        if (!(w6[i] > 0.0) || !std::isfinite(w6[i])) return fail(TL_EINVAL, "six-vertex thresholds: weight %d", i);
+    for (int idx = 0; idx < 16; ++idx) {
+        const int b[4] = {idx & 1, (idx >> 1) & 1, (idx >> 2) & 1, (idx >> 3) & 1};
+        const double wa = w6[kCorner[0][b[0]][0]] * w6[kCorner[1][b[1]][0]] * w6[kCorner[2][b[2]][0]] *
+                          w6[kCorner[3][b[3]][0]];
+        const double wb = w6[kCorner[0][b[0]][1]] * w6[kCorner[1][b[1]][1]] * w6[kCorner[2][b[2]][1]] *
+                          w6[kCorner[3][b[3]][1]];
+        t16[idx] = to_threshold(wb / (wa + wb));
+    }
+    return TL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chains
+// ---------------------------------------------------------------------------
+struct tl_chain {
+    tl_ctx* ctx = nullptr;
+    Geom g{};
+    uint64_t sites = 0;
+    int kappa = 0;
+    std::vector<uint8_t> cover;        // for validation of written states
+    std::vector<uint8_t> init;         // boundary reference (six-vertex)
+    tl_domain dom_copy;                // host copy of the domain description
+    uint32_t* rows = nullptr;          // packed state
+    uint32_t* rows0 = nullptr;         // packed starting state (for reset)
+    int2* grange = nullptr;
+    uint8_t* canon = nullptr;          // staging buffer [ntype][H][W]
+    uint32_t* tplanes = nullptr;       // per-site threshold planes
+    ThrView th{};
+    DevRng rng{};
+    uint64_t seed = 0;
+    uint32_t stream_id = 0;
+    uint64_t sweep = 0;
+    uint64_t launches = 0;
+    // observables
+    unsigned long long* hash = nullptr;
+    uint32_t* counts = nullptr;
+    uint64_t samples = 0;
+    uint32_t stride = 0;
+    uint64_t burn = 0;
+    bool density_on = false;
+    bool counts_dirty = false;         // counters to be zeroed on the next run's stream
+    int* hxlo = nullptr;
+    int* hxhi = nullptr;
+    int* hspine = nullptr;
+    int* hbase = nullptr;
+    int32_t* hscratch = nullptr;
+    // planner
+    int kernel = 0;
+    int spl = 0;
+};
+
+static void chain_free(tl_chain* c)
+{
+    if (!c) return;
+    cudaFree(c->rows);
+    cudaFree(c->rows0);
+    cudaFree(c->grange);
+    cudaFree(c->canon);
+    cudaFree(c->tplanes);
+    cudaFree(c->hash);
+    cudaFree(c->counts);
+    cudaFree(c->hxlo);
+    cudaFree(c->hxhi);
+    cudaFree(c->hspine);
+    cudaFree(c->hbase);
+    cudaFree(c->hscratch);
+    delete c;
+}
+
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cudaStream_t SS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <class T>
+static int dev_alloc(T** p, size_t count, const char* what)
+{
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA, "cudaMalloc(%s, %zu B): %s", what,
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
+    return TL_OK;
+}
+
+#define TL_TRY(expr)                   \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != TL_OK) return rc_;  \
+    } while (0)
+
+static int upload_state(tl_chain* c, const uint8_t* canon, bool device_src, void* stream)
+{
+    const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
+    CUDA_TRY(cudaMemcpyAsync(c->canon, canon, n, device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             SS(stream)));
+    CUDA_TRY(launch_pack(c->g, c->canon, c->rows, stream));
+    c->launches += 1;
+    return TL_OK;
+}
+
+TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon_init, uint64_t seed,
+                           uint32_t stream_id, const tl_thresholds* th, tl_chain** out)
+{
+    if (!ctx || !d || !th || !out) return fail(TL_EINVAL, "tl_chain_create: NULL argument");
+    const Geom& g = d->g;
+    if (g.lattice == LAT_SIXV && th->kind != TL_T_TABLE16)
+        return fail(TL_EINVAL, "tl_chain_create: six-vertex needs a 16-entry table");
+    if (g.lattice != LAT_SIXV && th->kind == TL_T_TABLE16)
+        return fail(TL_EINVAL, "tl_chain_create: 16-entry tables are for six-vertex only");
+    if (th->kind == TL_T_SITE && !th->site) return fail(TL_EINVAL, "tl_chain_create: per-site thresholds missing");
+    if (th->kind < 0 || th->kind > 2) return fail(TL_EINVAL, "tl_chain_create: bad threshold kind");
+    const uint8_t* start = canon_init ? canon_init : d->init.data();
+    if (canon_init) TL_TRY(validate(d, canon_init));
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    tl_chain* c = new (std::nothrow) tl_chain();
+    if (!c) return fail(TL_ENOMEM, "tl_chain_create: host allocation");
+    c->ctx = ctx;
+    c->g = g;
+    c->sites = d->sites;
+    c->kappa = d->kappa;
+    c->dom_copy = *d;
+    c->seed = seed;
+    c->stream_id = stream_id;
+    c->rng.k0 = (uint32_t)seed;
+    c->rng.k1 = (uint32_t)(seed >> 32);
+    c->rng.stream = stream_id;
+    int rc = TL_OK;
+    const size_t ncanon = (size_t)g.ntype * g.W * g.H;
+    if ((rc = dev_alloc(&c->rows, (size_t)g.total_words, "state")) ||
+        (rc = dev_alloc(&c->rows0, (size_t)g.total_words, "start state")) ||
+        (rc = dev_alloc(&c->grange, (size_t)g.H, "group ranges")) ||
+        (rc = dev_alloc(&c->canon, ncanon, "staging")) || (rc = dev_alloc(&c->hash, 1, "hash")) ||
+        (rc = dev_alloc(&c->hxlo, (size_t)d->hh, "height plan")) ||
+        (rc = dev_alloc(&c->hxhi, (size_t)d->hh, "height plan")) ||
+        (rc = dev_alloc(&c->hspine, (size_t)d->hh, "height plan")) ||
+        (rc = dev_alloc(&c->hbase, (size_t)d->hh, "height plan"))) {
+        chain_free(c);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(c->grange, d->grange.data(), sizeof(int2) * g.H, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->hxlo, d->hxlo.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->hxhi, d->hxhi.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->hspine, d->hspine.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        chain_free(c);
+        return fail(TL_ECUDA, "tl_chain_create: upload: %s", cudaGetErrorString(e));
+    }
+    // thresholds
+    c->th.kind = th->kind == TL_T_SITE ? THR_SITE : (th->kind == TL_T_TABLE16 ? THR_TABLE : THR_SCALAR);
+    c->th.scalar = th->scalar;
+    c->th.kmax = th->scalar ? 31 - __builtin_ctz(th->scalar) : -1;
+    c->th.planes = nullptr;
+    if (th->kind == TL_T_TABLE16) {
+        for (int k = 0; k < 32; ++k) {
+            uint32_t m = 0;
+            for (int idx = 0; idx < 16; ++idx) m |= ((th->table16[idx] >> (31 - k)) & 1u) << idx;
+            c->th.tmask[k] = m;
+        }
+    }
+    if (th->kind == TL_T_SITE) {
+        const size_t nplanes = (size_t)g.H * g.npar * 32 * g.K;
+        uint32_t* tdev = nullptr;
+        if ((rc = dev_alloc(&c->tplanes, nplanes, "threshold planes")) ||
+            (rc = dev_alloc(&tdev, (size_t)g.W * g.H, "thresholds"))) {
+            cudaFree(tdev);
+            chain_free(c);
+            return rc;
+        }
+        e = cudaMemcpy(tdev, th->site, sizeof(uint32_t) * g.W * g.H, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = (cudaError_t)launch_threshold_planes(g, tdev, c->tplanes, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(tdev);
+        if (e != cudaSuccess) {
+            chain_free(c);
+            return fail(TL_ECUDA, "tl_chain_create: threshold planes: %s", cudaGetErrorString(e));
+        }
+        c->th.planes = c->tplanes;
+        c->launches += 1;
+    }
+    rc = upload_state(c, start, false, nullptr);
+    if (rc == TL_OK) {
+        e = cudaMemcpyAsync(c->rows0, c->rows, (size_t)g.total_words * 4, cudaMemcpyDeviceToDevice, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) rc = fail(TL_ECUDA, "tl_chain_create: %s", cudaGetErrorString(e));
+    }
+    if (rc != TL_OK) {
+        chain_free(c);
+        return rc;
+    }
+    *out = c;
+    return TL_OK;
+}
+
+TL_API void tl_chain_destroy(tl_chain* c)
+{
+    if (c) cudaSetDevice(c->ctx->device);
+    chain_free(c);
+}
+
+TL_API int tl_chain_reset(tl_chain* c, void* stream)
+{
+    if (!c) return fail(TL_EINVAL, "tl_chain_reset: NULL chain");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    CUDA_TRY(cudaMemcpyAsync(c->rows, c->rows0, (size_t)c->g.total_words * 4, cudaMemcpyDeviceToDevice, SS(stream)));
+    c->sweep = 0;
+    c->density_on = false;
+    c->samples = 0;
+    return TL_OK;
+}
+
+TL_API uint64_t tl_chain_sweep(const tl_chain* c) { return c ? c->sweep : 0; }
+TL_API uint64_t tl_chain_launches(const tl_chain* c) { return c ? c->launches : 0; }
+
+TL_API int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch)
+{
+    if (!c || kernel < 0 || kernel > 2 || sweeps_per_launch < 0) return fail(TL_EINVAL, "tl_chain_set_plan: bad argument");
+    c->kernel = kernel;
+    c->spl = sweeps_per_launch;
+    return TL_OK;
+}
+
+// Sweeps [c->sweep, c->sweep + n) with no density sample inside.
+static int run_segment(tl_chain* c, uint64_t n, void* stream)
+{
+    const Geom& g = c->g;
+    for (uint64_t s = 0; s < n; ++s) {
+        const uint32_t sw = (uint32_t)(c->sweep + s);
+        for (int p = 0; p < g.passes; ++p) {
+            const int e = launch_pass_global(g, c->rows, (uint32_t)p, sw, c->rng, c->th, c->grange, stream);
+            if (e) return fail(TL_ECUDA, "pass kernel: %s", cudaGetErrorString((cudaError_t)e));
+        }
+        c->launches += (uint64_t)g.passes;
+    }
+    c->sweep += n;
+    return TL_OK;
+}
+
+static uint64_t next_sample(const tl_chain* c)
+{
+    // smallest s > sweep with s >= burn and (s - burn) % stride == 0
+    const uint64_t s0 = std::max<uint64_t>(c->burn, c->sweep + 1);
+    const uint64_t k = (s0 - c->burn + c->stride - 1) / c->stride;
+    return c->burn + k * c->stride;
+}
+
+static int take_sample(tl_chain* c, void* stream)
+{
+    const int e = launch_density_accumulate(c->g, c->rows, c->counts, stream);
+    if (e) return fail(TL_ECUDA, "density kernel: %s", cudaGetErrorString((cudaError_t)e));
+    c->samples += 1;
+    c->launches += 1;
+    return TL_OK;
+}
+
+TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
+{
+    if (!c) return fail(TL_EINVAL, "tl_run_sweeps: NULL chain");
+    if (c->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (c->counts_dirty) {
+        const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
+        CUDA_TRY(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), SS(stream)));
+        c->counts_dirty = false;
+    }
+    const uint64_t end = c->sweep + k;
+    while (c->sweep < end) {
+        uint64_t stop = end;
+        bool sample = false;
+        if (c->density_on) {
+            const uint64_t ns = next_sample(c);
+            if (ns <= end) {
+                stop = ns;
+                sample = true;
+            }
+        }
+        TL_TRY(run_segment(c, stop - c->sweep, stream));
+        if (sample) TL_TRY(take_sample(c, stream));
+    }
+    return TL_OK;
+}
+
+TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream)
+{
+    if (!c || (!ring && k)) return fail(TL_EINVAL, "tl_run_sweeps_hashed: NULL argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    const bool dev = k ? is_device_ptr(ring) : true;
+    uint64_t* dring = reinterpret_cast<uint64_t*>(ring);
+    uint64_t* tmp = nullptr;
+    if (!dev && k) {
+        TL_TRY(dev_alloc(&tmp, (size_t)k, "hash ring"));
+        dring = tmp;
+    }
+    int rc = TL_OK;
+    for (uint64_t i = 0; i < k && rc == TL_OK; ++i) {
+        rc = tl_run_sweeps(c, 1, stream);
+        if (rc == TL_OK) {
+            const int e = launch_hash(c->g, c->rows, reinterpret_cast<unsigned long long*>(dring + i), stream);
+            c->launches += 1;
+            if (e) rc = fail(TL_ECUDA, "hash kernel: %s", cudaGetErrorString((cudaError_t)e));
+        }
+    }
+    if (tmp) {
+        if (rc == TL_OK) {
+            cudaError_t e = cudaMemcpyAsync(ring, tmp, k * 8, cudaMemcpyDeviceToHost, SS(stream));
+            if (e == cudaSuccess) e = cudaStreamSynchronize(SS(stream));
+            if (e != cudaSuccess) rc = fail(TL_ECUDA, "hash ring copy: %s", cudaGetErrorString(e));
+        } else {
+            cudaStreamSynchronize(SS(stream));
+        }
+        cudaFree(tmp);
+    }
+    return rc;
+}
+
+TL_API int tl_read_state(tl_chain* c, uint8_t* canon, size_t cap, void* stream)
+{
+    if (!c || !canon) return fail(TL_EINVAL, "tl_read_state: NULL argument");
+    const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
+    if (cap < n) return fail(TL_EINVAL, "tl_read_state: cap %zu < %zu", cap, n);
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (is_device_ptr(canon)) {
+        CUDA_TRY(launch_unpack(c->g, c->rows, canon, stream));
+        c->launches += 1;
+        return TL_OK;
+    }
+    CUDA_TRY(launch_unpack(c->g, c->rows, c->canon, stream));
+    c->launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(canon, c->canon, n, cudaMemcpyDeviceToHost, SS(stream)));
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    return TL_OK;
+}
+
+TL_API int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* stream)
+{
+    if (!c || !canon) return fail(TL_EINVAL, "tl_write_state: NULL argument");
+    const size_t want = (size_t)c->g.ntype * c->g.W * c->g.H;
+    if (n != want) return fail(TL_EINVAL, "tl_write_state: n %zu != %zu", n, want);
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    const bool dev = is_device_ptr(canon);
+    std::vector<uint8_t> host;
+    const uint8_t* check = canon;
+    if (dev) {
+        host.resize(n);
+        CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+        CUDA_TRY(cudaMemcpy(host.data(), canon, n, cudaMemcpyDeviceToHost));
+        check = host.data();
+    }
+    TL_TRY(validate(&c->dom_copy, check));
+    TL_TRY(upload_state(c, canon, dev, stream));
+    if (!dev) CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    return TL_OK;
+}
+
+TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_state_hash: NULL argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (is_device_ptr(out)) {
+        CUDA_TRY(launch_hash(c->g, c->rows, reinterpret_cast<unsigned long long*>(out), stream));
+        c->launches += 1;
+        return TL_OK;
+    }
+    CUDA_TRY(launch_hash(c->g, c->rows, c->hash, stream));
+    c->launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(out, c->hash, 8, cudaMemcpyDeviceToHost, SS(stream)));
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    return TL_OK;
+}
+
+TL_API int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_read_height: NULL argument");
+    const tl_domain& d = c->dom_copy;
+    const size_t n = (size_t)d.hw * d.hh;
+    if (cap < n) return fail(TL_EINVAL, "tl_read_height: cap %zu < %zu", cap, n);
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    int32_t* dst = out;
+    const bool dev = is_device_ptr(out);
+    if (!dev) {
+        if (!c->hscratch) TL_TRY(dev_alloc(&c->hscratch, n, "height scratch"));
+        dst = c->hscratch;
+    }
+    const int e = launch_height(c->g, c->rows, c->hxlo, c->hxhi, c->hspine, d.hw, d.hh, dst, c->hbase, stream);
+    if (e) return fail(TL_ECUDA, "height kernels: %s", cudaGetErrorString((cudaError_t)e));
+    c->launches += 3;
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(out, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, SS(stream)));
+        CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    }
+    return TL_OK;
+}
+
+TL_API int tl_density_begin(tl_chain* c, uint32_t stride, uint64_t burn_in)
+{
+    if (!c || stride == 0) return fail(TL_EINVAL, "tl_density_begin: bad argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
+    if (!c->counts) TL_TRY(dev_alloc(&c->counts, n, "density counters"));
+    c->counts_dirty = true;
+    c->samples = 0;
+    c->stride = stride;
+    c->burn = burn_in;
+    c->density_on = true;
+    return TL_OK;
+}
+
+template <class F>
+static int to_output(tl_chain* c, double* out, size_t n, void* stream, F launch)
+{
+    if (is_device_ptr(out)) {
+        const int e = launch(out);
+        if (e) return fail(TL_ECUDA, "density kernel: %s", cudaGetErrorString((cudaError_t)e));
+        c->launches += 1;
+        return TL_OK;
+    }
+    double* tmp = nullptr;
+    TL_TRY(dev_alloc(&tmp, n, "density output"));
+    int e = launch(tmp);
+    c->launches += 1;
+    if (!e) e = cudaMemcpyAsync(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, SS(stream));
+    if (!e) e = cudaStreamSynchronize(SS(stream));
+    cudaFree(tmp);
+    if (e) return fail(TL_ECUDA, "density readback: %s", cudaGetErrorString((cudaError_t)e));
+    return TL_OK;
+}
+
+TL_API int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* samples, void* stream)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_read_density: NULL argument");
+    if (!c->counts) return fail(TL_EINVAL, "tl_read_density: tl_density_begin was not called");
+    const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
+    if (cap < n) return fail(TL_EINVAL, "tl_read_density: cap %zu < %zu", cap, n);
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (samples) *samples = c->samples;
+    return to_output(c, out, n, stream, [&](double* o) {
+        return launch_density_read(c->counts, n, c->samples, o, stream);
+    });
+}
+
+TL_API int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_read_domino_nsew: NULL argument");
+    if (c->g.lattice != LAT_DOMINO) return fail(TL_EINVAL, "tl_read_domino_nsew: not a domino chain");
+    if (!c->counts) return fail(TL_EINVAL, "tl_read_domino_nsew: tl_density_begin was not called");
+    const size_t n = (size_t)4 * (c->g.W - 1) * (c->g.H - 1);
+    if (cap < n) return fail(TL_EINVAL, "tl_read_domino_nsew: cap %zu < %zu", cap, n);
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    return to_output(c, out, n, stream, [&](double* o) {
+        return launch_nsew(c->g, c->counts, c->samples, c->kappa, o, stream);
+    });
+}

@@ -1,0 +1,98 @@
+// Internal declarations shared by the host runtime (tl_host.cpp) and the CUDA
+// kernels (tl_kernels.cu).  Not part of the public C-ABI.
+//
+// Packed device layout of one chain ("rows"):
+//   for every vertex row y of the box (plus one zero pad row below and one
+//   above), P bit planes of K uint32 words each, plane = type * npar + res.
+//   Bit j of a plane row holds the edge of type `type` at x = npar * j + res:
+//     dominoes    npar 2, types {Hz, Vt}          (P = 4)
+//     lozenges    npar 3, types {E1, E2, E3}      (P = 9)
+//     six-vertex  npar 2, types {Hz, Vt}          (P = 4)
+//   so every word holds 32 sites of one colour class of one row, and a
+//   128-site group (4 words) is exactly one Philox4x32 output of the keying.
+//   K = (j values per row rounded up to 128) / 32.  Rows are 16-byte
+//   aligned; word (y, plane, k) lives at rows[((y + 1) * P + plane) * K + k].
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace tl {
+
+enum Lattice : int { LAT_DOMINO = 0, LAT_LOZENGE = 1, LAT_SIXV = 2 };
+enum ThrKind : int { THR_SCALAR = 0, THR_SITE = 1, THR_TABLE = 2 };
+
+struct Geom {
+    int lattice;
+    int W, H;        // vertex box
+    int N;           // six-vertex size (W = H = N + 2), else 0
+    int npar;        // x residues per plane type
+    int ntype;       // plane types
+    int P;           // planes per row
+    int K;           // words per plane row (multiple of 4)
+    int Kg;          // 128-site groups per row (K / 4)
+    int passes;      // colour classes per sweep
+    int64_t row_words;   // P * K
+    int64_t total_words; // (H + 2) * row_words
+};
+
+struct DevRng {
+    uint32_t k0, k1;      // Philox key = seed
+    uint32_t stream;
+};
+
+struct ThrView {
+    int kind;               // ThrKind
+    uint32_t scalar;        // THR_SCALAR
+    int kmax;               // last plane that can decide a scalar compare
+    const uint32_t* planes; // THR_SITE: [H][npar][32][K] threshold bit planes
+    uint32_t tmask[32];     // THR_TABLE: bit idx of tmask[k] = bit 31-k of t16[idx]
+};
+
+// Height propagation plan (per height-grid row): domain interval
+// [xlo, xhi] (empty if xlo > xhi) and the spine column linking the row to
+// the previous non-empty one (-1 for the first).
+struct HeightPlan {
+    int hw, hh;
+};
+
+// ---- kernel launchers (tl_kernels.cu); all return cudaError_t as int ----
+int launch_pack(const Geom& g, const uint8_t* canon_dev, uint32_t* rows, void* stream);
+int launch_unpack(const Geom& g, const uint32_t* rows, uint8_t* canon_dev, void* stream);
+int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t sweep,
+                       const DevRng& rng, const ThrView& th, const int2* grange,
+                       void* stream);
+int launch_hash(const Geom& g, const uint32_t* rows, unsigned long long* out, void* stream);
+int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* counts, void* stream);
+int launch_density_read(const uint32_t* counts, uint64_t n, uint64_t samples, double* out,
+                        void* stream);
+int launch_nsew(const Geom& g, const uint32_t* counts, uint64_t samples, int kappa, double* out,
+                void* stream);
+int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi,
+                  const int* spine, int hw, int hh, int32_t* out, int* base_scratch,
+                  void* stream);
+int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t* planes,
+                            void* stream);
+
+// Resident multi-sweep kernel: one cooperative launch runs `nsweeps` sweeps
+// starting at absolute sweep `sweep0` with the state held in shared memory.
+struct ResidentPlan {
+    int ctas;            // cooperative grid size
+    int threads;         // threads per CTA
+    int halo;            // passes per exchange cycle (= halo rows per side)
+    int max_rows;        // rows of a stripe (without halos)
+    size_t smem_bytes;   // dynamic shared memory per CTA
+    const int* stripe_lo;   // device [ctas+1]: stripe c owns rows [lo[c], lo[c+1])
+    uint32_t* xbuf;         // device exchange buffer
+    unsigned int* flags;    // device [ctas] progress flags
+    int* status;            // device error word (0 = ok)
+};
+int resident_query(const Geom& g, int device, int threads, int halo, int* ctas_per_sm,
+                   size_t* smem_per_row);
+int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
+                    uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
+                    unsigned int epoch, void* stream);
+
+}  // namespace tl

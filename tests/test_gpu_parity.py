@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+The chain is a deterministic function of (domain, start, thresholds, seed,
+stream, sweep index), so the packed GPU state must equal the oracle's state
+bit for bit after every sweep.  Sizes span several 128-site groups with a
+ragged tail, the smallest domains, extreme thresholds, and the full benchmark
+sizes (sampled: the first sweeps in full, then invariants).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SQ2 = [1, 1, 1, 1, math.sqrt(2), math.sqrt(2)]
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_07250_gb300 as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.Context(0)
+
+
+def _domain(T, kind, args):
+    return {"aztec": T.Domain.aztec, "rect": T.Domain.rect, "hex": T.Domain.hexagon,
+            "dwbc": T.Domain.dwbc}[kind](*args)
+
+
+def _oracle_state(kind, args):
+    return {"aztec": O.aztec, "rect": O.rect, "hex": O.hexagon, "dwbc": O.dwbc}[kind](*args)
+
+
+def _lat(kind):
+    return {"aztec": O.DOMINO, "rect": O.DOMINO, "hex": O.LOZENGE, "dwbc": O.SIXV}[kind]
+
+
+def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, scalar=None,
+              site=None, w6=None, hashed=True):
+    dom = _domain(T, kind, args)
+    lat = _lat(kind)
+    if lat == O.SIXV:
+        t16 = O.sixv_thresholds(w6)
+        th = T.thresholds(table16=t16)
+        okw = dict(t16=t16)
+    elif site is not None:
+        th = T.thresholds(site=site)
+        okw = dict(t_site=site)
+    else:
+        th = T.thresholds(scalar=scalar)
+        okw = dict(t_scalar=scalar)
+    ch = T.Chain(ctx, dom, seed=seed, stream_id=stream, th=th)
+    if kernel or spl:
+        ch.set_plan(kernel, spl)
+    st = _oracle_state(kind, args)
+    if hashed:
+        ring = ch.run_hashed(k)
+        ohash = O.sweeps(lat, st, seed=seed, stream=stream, k=k, want_hashes=True, **okw)
+        bad = np.nonzero(ring != ohash)[0]
+        assert bad.size == 0, "first mismatch at sweep %d" % bad[0]
+    else:
+        ch.run(k)
+        O.sweeps(lat, st, seed=seed, stream=stream, k=k, **okw)
+    got = ch.read_state()
+    assert np.array_equal(got, st)
+    assert ch.state_hash() == O.state_hash(st)
+    assert ch.sweep == k
+    return ch, st
+
+
+# ---------------------------------------------------------------------------
+# Bit-exact trajectories
+# ---------------------------------------------------------------------------
+def test_aztec32_uniform_every_sweep_full_length(T, ctx):
+    # Aztec diamond n = 32, seed 1, t = 2^31, 10^4 sweeps, hash after every sweep
+    _run_pair(T, ctx, "aztec", (32,), seed=1, k=10_000, scalar=1 << 31)
+
+
+@pytest.mark.parametrize("kind,args", [
+    ("aztec", (1,)), ("aztec", (2,)), ("aztec", (63,)), ("aztec", (64,)), ("aztec", (129,)),
+    ("rect", (2, 2)), ("rect", (300, 7)), ("rect", (255, 9)), ("rect", (7, 40)),
+])
+def test_domino_uniform_sizes(T, ctx, kind, args):
+    _run_pair(T, ctx, kind, args, seed=12345, stream=3, k=60, scalar=1 << 31)
+
+
+@pytest.mark.parametrize("t", [0, 1, (1 << 31) - 1, (1 << 31) + 1, 0xC0000000, 0xFFFFFFFF, 123456789])
+def test_domino_scalar_thresholds(T, ctx, t):
+    _run_pair(T, ctx, "aztec", (40,), seed=99, k=30, scalar=t)
+
+
+@pytest.mark.parametrize("n", [5, 37, 100])
+def test_domino_edge_weights(T, ctx, n):
+    rng = np.random.default_rng(n)
+    W = 2 * n + 1
+    w = np.exp(0.5 * rng.standard_normal((2, W, W)))
+    t = O.domino_thresholds(w)
+    _run_pair(T, ctx, "aztec", (n,), seed=3, stream=n, k=40, site=t)
+
+
+@pytest.mark.parametrize("abc", [(1, 1, 1), (2, 3, 4), (20, 9, 33), (150, 200, 130)])
+def test_lozenge_q(T, ctx, abc):
+    ta, _ = O.lozenge_thresholds(0.9995)
+    _run_pair(T, ctx, "hex", abc, seed=11, k=40, scalar=ta)
+
+
+def test_lozenge_site_thresholds(T, ctx):
+    a, b, c = 30, 41, 25
+    rng = np.random.default_rng(7)
+    st = O.hexagon(a, b, c)
+    t = rng.integers(0, 1 << 32, size=st.shape[1:], dtype=np.uint64).astype(np.uint32)
+    _run_pair(T, ctx, "hex", (a, b, c), seed=5, k=40, site=t)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 11, 260, 301])
+def test_sixv_dwbc_sqrt2(T, ctx, N):
+    _run_pair(T, ctx, "dwbc", (N,), seed=11, k=50, w6=SQ2)
+
+
+@pytest.mark.parametrize("w6", [[1] * 6, [1, 1, 1, 1, math.sqrt(8), math.sqrt(8)],
+                                [0.7, 1.3, 0.4, 1.9, 1.1, 0.6]])
+def test_sixv_weights(T, ctx, w6):
+    _run_pair(T, ctx, "dwbc", (130,), seed=2, stream=9, k=40, w6=w6)
+
+
+def test_results_do_not_depend_on_how_sweeps_are_split(T, ctx):
+    dom = T.Domain.aztec(50)
+    a = T.Chain(ctx, dom, seed=8, th=T.thresholds(scalar=1 << 31))
+    b = T.Chain(ctx, dom, seed=8, th=T.thresholds(scalar=1 << 31))
+    a.run(100)
+    for k in (1, 2, 3, 7, 87):
+        b.run(k)
+    assert a.state_hash() == b.state_hash()
+    c = T.Chain(ctx, dom, seed=9, th=T.thresholds(scalar=1 << 31))
+    c.run(100)
+    assert c.state_hash() != a.state_hash()
+
+
+# ---------------------------------------------------------------------------
+# Full benchmark sizes: the first sweeps bit-exact in full
+# ---------------------------------------------------------------------------
+def test_aztec2048_first_sweeps(T, ctx):
+    _run_pair(T, ctx, "aztec", (2048,), seed=7, k=12, scalar=1 << 31, hashed=True)
+
+
+def test_hexagon1024_first_sweeps(T, ctx):
+    ta, _ = O.lozenge_thresholds(0.9995)
+    _run_pair(T, ctx, "hex", (1024, 1024, 1024), seed=11, k=8, scalar=ta)
+
+
+def test_dwbc2048_first_sweeps(T, ctx):
+    _run_pair(T, ctx, "dwbc", (2048,), seed=11, k=8, w6=SQ2)
+
+
+# ---------------------------------------------------------------------------
+# Observables
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,args", [("aztec", (45,)), ("rect", (33, 20)), ("hex", (17, 23, 30)),
+                                       ("dwbc", (70,))])
+def test_height_matches_oracle(T, ctx, kind, args):
+    lat = _lat(kind)
+    kw = dict(w6=SQ2) if lat == O.SIXV else dict(scalar=1 << 31)
+    ch, st = _run_pair(T, ctx, kind, args, seed=21, k=25, hashed=False, **kw)
+    h = ch.read_height()
+    ho, bad = O.height(lat, st)
+    assert bad == 0
+    assert np.array_equal(h, ho)
+
+
+def test_density_matches_oracle(T, ctx):
+    n = 20
+    dom = T.Domain.aztec(n)
+    ch = T.Chain(ctx, dom, seed=4, th=T.thresholds(scalar=1 << 31))
+    ch.density_begin(stride=3, burn_in=10)
+    ch.run(17)
+    ch.run(40)
+    dens, samples = ch.read_density()
+    st = O.aztec(n)
+    counts = np.zeros(st.shape, dtype=np.uint32)
+    nsamp = 0
+    for s in range(57):
+        O.sweeps(O.DOMINO, st, seed=4, sweep0=s, k=1, t_scalar=1 << 31)
+        done = s + 1
+        if done >= 10 and (done - 10) % 3 == 0:
+            O.accumulate(st, counts)
+            nsamp += 1
+    assert samples == nsamp
+    assert np.array_equal(dens, counts / nsamp)
+    nsew = ch.read_nsew()
+    # every domain face is covered by exactly one domino type per sample
+    faces = nsew.sum(0)
+    W = 2 * n
+    for y in range(W):
+        for x in range(W):
+            inside = abs(x + 0.5 - n) + abs(y + 0.5 - n) <= n
+            assert faces[y, x] == pytest.approx(1.0 if inside else 0.0, abs=1e-12)
+
+
+def test_read_write_state_round_trip_and_validation(T, ctx):
+    dom = T.Domain.hexagon(9, 8, 7)
+    ch = T.Chain(ctx, dom, seed=1, th=T.thresholds(scalar=1 << 31))
+    ch.run(30)
+    s = ch.read_state()
+    ch2 = T.Chain(ctx, dom, seed=1, th=T.thresholds(scalar=1 << 31), init=s)
+    assert ch2.state_hash() == ch.state_hash()
+    bad = s.copy()
+    bad[0, 5, 5] ^= 1
+    with pytest.raises(T.TilingError) as e:
+        ch.write_state(bad)
+    assert e.value.code == T.TL_EINVAL
+    ch.write_state(O.hexagon(9, 8, 7))
+    assert ch.state_hash() == O.state_hash(O.hexagon(9, 8, 7))
+
+
+def test_device_buffers(T, ctx):
+    import torch
+    dom = T.Domain.aztec(30)
+    ch = T.Chain(ctx, dom, seed=5, th=T.thresholds(scalar=1 << 31))
+    stream = torch.cuda.Stream()
+    ch.run(10, stream=stream)
+    out = torch.zeros(dom.canon_shape, dtype=torch.uint8, device="cuda")
+    ch.read_state(out, stream=stream)
+    hbuf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ch.state_hash(out=hbuf, stream=stream)
+    stream.synchronize()
+    st = O.aztec(30)
+    O.sweeps(O.DOMINO, st, seed=5, k=10, t_scalar=1 << 31)
+    assert np.array_equal(out.cpu().numpy(), st)
+    assert int(hbuf.cpu().numpy().view(np.uint64)[0]) == O.state_hash(st)
