@@ -4,7 +4,7 @@ Glauber dynamics (Keating & Sridhar, "Random Tilings with the GPU").
 Thin ctypes binding over ``libtiling.so`` (the C-ABI in ``include/tiling.h``):
 argument marshalling only.  Every step of the sampler runs in the library's
 CUDA kernels; there is no CPU fallback, and importing this package fails if
-the library has not been built (``paper_1804_07250_gb300._build.build()``).
+the library has not been built (``python paper_1804_07250_gb300/_build.py``).
 
 Buffers may be numpy arrays (host) or torch tensors (host or CUDA); streams
 may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer or None (the
@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtiling.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libtiling.so is missing: build it with "
-                      "`python -m paper_1804_07250_gb300._build` (needs nvcc)")
+                      "`python paper_1804_07250_gb300/_build.py` (needs nvcc)")
 
 _lib = ctypes.CDLL(LIB_PATH)
 

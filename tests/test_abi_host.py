@@ -21,8 +21,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def T():
-    from paper_1804_07250_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_1804_07250_gb300 as T
     return T
 
