@@ -270,11 +270,18 @@ int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* samples, voi
  * (so the all-horizontal start is north in the upper half) and 0 otherwise. */
 int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream);
 
-/* Launch-planner controls (for tests and tuning): sweeps per launch of the
- * resident kernel (0 = automatic) and the kernel family: 0 automatic, 1 the
- * one-launch-per-pass global-memory kernel, 2 the shared-memory resident
- * multi-sweep kernel.  Results do not depend on either. */
-int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch);
+/* Launch-planner controls (for tests and tuning).  kernel: 0 automatic, 1
+ * the one-launch-per-pass global-memory kernel, 2 the shared-memory resident
+ * multi-sweep kernel (TL_EUNSUPPORTED if the domain does not fit it).
+ * sweeps_per_launch: cap on sweeps per resident launch (0 = no cap).  halo:
+ * passes between boundary exchanges of the resident kernel (0 = automatic,
+ * at most 64).  Results do not depend on any of them. */
+int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch, int halo);
+
+/* Wait for the chain's work on `stream` and report a failure of the
+ * resident kernel's bounded waits (TL_ETIMEOUT; the state is then
+ * undefined and should be rewritten with tl_write_state or tl_chain_reset). */
+int tl_chain_sync(tl_chain* c, void* stream);
 
 /* Count of kernel launches the library made on this chain since creation
  * (all kinds).  For accounting in benchmarks. */

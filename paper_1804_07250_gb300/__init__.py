@@ -77,7 +77,8 @@ _SIG = {
     "tl_chain_reset": (_i, [_vp, _vp]),
     "tl_chain_sweep": (_u64, [_vp]),
     "tl_chain_launches": (_u64, [_vp]),
-    "tl_chain_set_plan": (_i, [_vp, _i, _i]),
+    "tl_chain_set_plan": (_i, [_vp, _i, _i, _i]),
+    "tl_chain_sync": (_i, [_vp, _vp]),
     "tl_run_sweeps": (_i, [_vp, _u64, _vp]),
     "tl_run_sweeps_hashed": (_i, [_vp, _u64, _vp, _vp]),
     "tl_read_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -262,8 +263,12 @@ class Chain:
     def reset(self, stream=None):
         _check(_lib.tl_chain_reset(self._h, _stream(stream)))
 
-    def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0):
-        _check(_lib.tl_chain_set_plan(self._h, kernel, sweeps_per_launch))
+    def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0):
+        """kernel 0 auto / 1 per-pass global / 2 resident; results never depend on it."""
+        _check(_lib.tl_chain_set_plan(self._h, kernel, sweeps_per_launch, halo))
+
+    def sync(self, stream=None):
+        _check(_lib.tl_chain_sync(self._h, _stream(stream)))
 
     def run(self, k: int, stream=None):
         _check(_lib.tl_run_sweeps(self._h, k, _stream(stream)))

@@ -579,6 +579,15 @@ struct tl_chain {
     // planner
     int kernel = 0;
     int spl = 0;
+    int halo_req = 0;
+    bool res_ready = false, res_failed = false;
+    ResidentPlan res{};
+    int* stripe_d = nullptr;
+    uint32_t* xbuf_d = nullptr;
+    unsigned long long* flags_d = nullptr;
+    int* status_d = nullptr;
+    unsigned int epoch = 0;
+    std::string res_why;
 };
 
 static void chain_free(tl_chain* c)
@@ -596,6 +605,10 @@ static void chain_free(tl_chain* c)
     cudaFree(c->hspine);
     cudaFree(c->hbase);
     cudaFree(c->hscratch);
+    cudaFree(c->stripe_d);
+    cudaFree(c->xbuf_d);
+    cudaFree(c->flags_d);
+    cudaFree(c->status_d);
     delete c;
 }
 
@@ -753,15 +766,35 @@ TL_API int tl_chain_reset(tl_chain* c, void* stream)
 TL_API uint64_t tl_chain_sweep(const tl_chain* c) { return c ? c->sweep : 0; }
 TL_API uint64_t tl_chain_launches(const tl_chain* c) { return c ? c->launches : 0; }
 
-TL_API int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch)
+static bool want_resident(tl_chain* c);
+
+TL_API int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch, int halo)
 {
-    if (!c || kernel < 0 || kernel > 2 || sweeps_per_launch < 0) return fail(TL_EINVAL, "tl_chain_set_plan: bad argument");
+    if (!c || kernel < 0 || kernel > 2 || sweeps_per_launch < 0 || halo < 0 || halo > 64)
+        return fail(TL_EINVAL, "tl_chain_set_plan: bad argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
     c->kernel = kernel;
     c->spl = sweeps_per_launch;
+    if (halo != c->halo_req) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(c->stripe_d);
+        cudaFree(c->xbuf_d);
+        cudaFree(c->flags_d);
+        cudaFree(c->status_d);
+        c->stripe_d = nullptr;
+        c->xbuf_d = nullptr;
+        c->flags_d = nullptr;
+        c->status_d = nullptr;
+        c->res_ready = c->res_failed = false;
+        c->halo_req = halo;
+    }
+    if (kernel == 2 && !want_resident(c))
+        return fail(TL_EUNSUPPORTED, "resident kernel unavailable: %s", c->res_why.c_str());
     return TL_OK;
 }
 
-// Sweeps [c->sweep, c->sweep + n) with no density sample inside.
+// Sweeps [c->sweep, c->sweep + n) with no density sample inside, one launch
+// per pass over global memory.
 static int run_segment(tl_chain* c, uint64_t n, void* stream)
 {
     const Geom& g = c->g;
@@ -785,6 +818,12 @@ static uint64_t next_sample(const tl_chain* c)
     return c->burn + k * c->stride;
 }
 
+// Number of sample points s <= x (s = sweeps done, s >= burn, stride apart).
+static uint64_t samples_upto(const tl_chain* c, uint64_t x)
+{
+    return x >= c->burn ? (x - c->burn) / c->stride + 1 : 0;
+}
+
 static int take_sample(tl_chain* c, void* stream)
 {
     const int e = launch_density_accumulate(c->g, c->rows, c->counts, stream);
@@ -794,16 +833,131 @@ static int take_sample(tl_chain* c, void* stream)
     return TL_OK;
 }
 
-TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
+// Default halo depth (passes per exchange) of the resident kernel.
+static int default_halo(const Geom& g)
 {
-    if (!c) return fail(TL_EINVAL, "tl_run_sweeps: NULL chain");
-    if (c->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32");
-    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    return g.lattice == LAT_DOMINO ? 8 : (g.lattice == LAT_LOZENGE ? 6 : 8);
+}
+
+// Stripe partition, shared-memory budget and buffers of the resident kernel.
+static int plan_resident(tl_chain* c)
+{
+    const Geom& g = c->g;
+    const tl_domain& d = c->dom_copy;
+    const int h = c->halo_req > 0 ? c->halo_req : default_halo(g);
+    const int threads = 512;
+    // weight of a row: its active groups plus a fixed cost per row
+    std::vector<double> w(g.H, 0.0);
+    double total = 0;
+    for (int y = 0; y < g.H; ++y) {
+        const int2 r = d.grange[y];
+        w[y] = 0.25 + std::max(0, r.y - r.x);
+        total += w[y];
+    }
+    int C = std::min(c->ctx->sms, g.H / h);
+    if (C < 2) {
+        c->res_why = "domain too small for stripes";
+        return TL_EUNSUPPORTED;
+    }
+    for (;;) {
+        std::vector<int> lo(C + 1, 0);
+        double acc = 0;
+        int y = 0;
+        for (int k = 1; k < C; ++k) {
+            const double target = total * k / C;
+            const int ymin = lo[k - 1] + h;
+            const int ymax = g.H - h * (C - k);
+            while (y < g.H && (acc < target || y < ymin)) acc += w[y++];
+            y = std::min(std::max(y, ymin), ymax);
+            acc = 0;
+            for (int t = 0; t < y; ++t) acc += w[t];
+            lo[k] = y;
+        }
+        lo[C] = g.H;
+        int maxrows = 0;
+        for (int k = 0; k < C; ++k) maxrows = std::max(maxrows, lo[k + 1] - lo[k]);
+        const size_t smem = (size_t)(maxrows + 2 * h + 2) * (size_t)g.row_words * 4;
+        if ((long)smem > (long)c->ctx->smem_optin) {
+            c->res_why = "stripe does not fit in shared memory";
+            return TL_EUNSUPPORTED;
+        }
+        int bps = 0;
+        if (resident_prepare(g, c->th.kind, threads, smem, &bps) != 0 || bps < 1) {
+            c->res_why = "resident kernel does not fit on an SM";
+            return TL_EUNSUPPORTED;
+        }
+        if (C > bps * c->ctx->sms) {
+            C = bps * c->ctx->sms;
+            continue;
+        }
+        int rc;
+        if ((rc = dev_alloc(&c->stripe_d, (size_t)C + 1, "stripes")) ||
+            (rc = dev_alloc(&c->xbuf_d, (size_t)C * 4 * h * g.row_words, "exchange buffer")) ||
+            (rc = dev_alloc(&c->flags_d, (size_t)C, "flags")) || (rc = dev_alloc(&c->status_d, 1, "status")))
+            return rc;
+        CUDA_TRY(cudaMemcpy(c->stripe_d, lo.data(), sizeof(int) * (C + 1), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemset(c->flags_d, 0, sizeof(unsigned long long) * C));
+        CUDA_TRY(cudaMemset(c->status_d, 0, sizeof(int)));
+        c->res.ctas = C;
+        c->res.threads = threads;
+        c->res.halo = h;
+        c->res.smem_bytes = smem;
+        c->res.stripe_lo = c->stripe_d;
+        c->res.xbuf = c->xbuf_d;
+        c->res.flags = c->flags_d;
+        c->res.status = c->status_d;
+        c->res_ready = true;
+        return TL_OK;
+    }
+}
+
+static bool want_resident(tl_chain* c)
+{
+    if (c->kernel == 1) return false;
+    if (!c->res_ready && !c->res_failed) {
+        if (plan_resident(c) != TL_OK) c->res_failed = true;
+    }
+    return c->res_ready;
+}
+
+// Resident launches over [c->sweep, c->sweep + k), at most spl sweeps each.
+static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void* stream)
+{
+    uint64_t done = 0;
+    while (done < k) {
+        const uint64_t n = c->spl > 0 ? std::min<uint64_t>((uint64_t)c->spl, k - done) : k - done;
+        const bool dens = c->density_on;
+        const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
+                                      c->grange, ++c->epoch, ring ? ring + done : nullptr,
+                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, stream);
+        if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
+        if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
+        c->sweep += n;
+        c->launches += 1;
+        done += n;
+    }
+    return TL_OK;
+}
+
+static int zero_counts_if_needed(tl_chain* c, void* stream)
+{
     if (c->counts_dirty) {
         const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
         CUDA_TRY(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), SS(stream)));
         c->counts_dirty = false;
     }
+    return TL_OK;
+}
+
+TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
+{
+    if (!c) return fail(TL_EINVAL, "tl_run_sweeps: NULL chain");
+    if (c->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(zero_counts_if_needed(c, stream));
+    if (k == 0) return TL_OK;
+    if (want_resident(c)) return run_resident(c, k, nullptr, stream);
+    if (c->kernel == 2) return fail(TL_EUNSUPPORTED, "resident kernel unavailable: %s", c->res_why.c_str());
     const uint64_t end = c->sweep + k;
     while (c->sweep < end) {
         uint64_t stop = end;
@@ -821,6 +975,22 @@ TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
     return TL_OK;
 }
 
+TL_API int tl_chain_sync(tl_chain* c, void* stream)
+{
+    if (!c) return fail(TL_EINVAL, "tl_chain_sync: NULL chain");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    if (c->status_d) {
+        int st = 0;
+        CUDA_TRY(cudaMemcpy(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) {
+            CUDA_TRY(cudaMemset(c->status_d, 0, sizeof(int)));
+            return fail(TL_ETIMEOUT, "a bounded wait in the resident kernel gave up; chain state undefined");
+        }
+    }
+    return TL_OK;
+}
+
 TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream)
 {
     if (!c || (!ring && k)) return fail(TL_EINVAL, "tl_run_sweeps_hashed: NULL argument");
@@ -833,6 +1003,14 @@ TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* s
         dring = tmp;
     }
     int rc = TL_OK;
+    if (k && want_resident(c)) {
+        rc = zero_counts_if_needed(c, stream);
+        cudaError_t e = cudaMemsetAsync(dring, 0, k * 8, SS(stream));
+        if (rc == TL_OK && e != cudaSuccess) rc = fail(TL_ECUDA, "hash ring: %s", cudaGetErrorString(e));
+        if (rc == TL_OK) rc = run_resident(c, k, reinterpret_cast<unsigned long long*>(dring), stream);
+        k = rc == TL_OK ? k : 0;
+        goto copy_back;
+    }
     for (uint64_t i = 0; i < k && rc == TL_OK; ++i) {
         rc = tl_run_sweeps(c, 1, stream);
         if (rc == TL_OK) {
@@ -841,6 +1019,7 @@ TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* s
             if (e) rc = fail(TL_ECUDA, "hash kernel: %s", cudaGetErrorString((cudaError_t)e));
         }
     }
+copy_back:
     if (tmp) {
         if (rc == TL_OK) {
             cudaError_t e = cudaMemcpyAsync(ring, tmp, k * 8, cudaMemcpyDeviceToHost, SS(stream));
@@ -973,6 +1152,7 @@ TL_API int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* sampl
     const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
     if (cap < n) return fail(TL_EINVAL, "tl_read_density: cap %zu < %zu", cap, n);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(zero_counts_if_needed(c, stream));
     if (samples) *samples = c->samples;
     return to_output(c, out, n, stream, [&](double* o) {
         return launch_density_read(c->counts, n, c->samples, o, stream);
@@ -987,6 +1167,7 @@ TL_API int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* strea
     const size_t n = (size_t)4 * (c->g.W - 1) * (c->g.H - 1);
     if (cap < n) return fail(TL_EINVAL, "tl_read_domino_nsew: cap %zu < %zu", cap, n);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(zero_counts_if_needed(c, stream));
     return to_output(c, out, n, stream, [&](double* o) {
         return launch_nsew(c->g, c->counts, c->samples, c->kappa, o, stream);
     });

@@ -76,23 +76,34 @@ int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int
 int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t* planes,
                             void* stream);
 
-// Resident multi-sweep kernel: one cooperative launch runs `nsweeps` sweeps
-// starting at absolute sweep `sweep0` with the state held in shared memory.
+// Resident multi-sweep kernel.  One cooperative launch runs `nsweeps`
+// sweeps from absolute sweep `sweep0`.  CTA c owns the rows
+// [stripe_lo[c], stripe_lo[c+1]) and keeps them, plus `halo` rows on each
+// side, in shared memory for the whole launch.  Every `halo` passes the
+// CTAs publish their boundary rows and read their neighbours' (double
+// buffered, ordered by per-CTA progress flags); in between, the halo rows
+// are recomputed redundantly, the valid region shrinking by one row per pass.
 struct ResidentPlan {
-    int ctas;            // cooperative grid size
-    int threads;         // threads per CTA
-    int halo;            // passes per exchange cycle (= halo rows per side)
-    int max_rows;        // rows of a stripe (without halos)
-    size_t smem_bytes;   // dynamic shared memory per CTA
-    const int* stripe_lo;   // device [ctas+1]: stripe c owns rows [lo[c], lo[c+1])
-    uint32_t* xbuf;         // device exchange buffer
-    unsigned int* flags;    // device [ctas] progress flags
-    int* status;            // device error word (0 = ok)
+    int ctas;                      // cooperative grid size
+    int threads;                   // threads per CTA
+    int halo;                      // passes per exchange cycle (= halo rows per side)
+    size_t smem_bytes;             // dynamic shared memory per CTA
+    const int* stripe_lo;          // device [ctas + 1]
+    uint32_t* xbuf;                // device [ctas][2][2][halo][row_words]
+    unsigned long long* flags;     // device [ctas] progress flags (epoch << 32 | cycle)
+    int* status;                   // device error word: 0 ok, 1 a bounded wait gave up
 };
-int resident_query(const Geom& g, int device, int threads, int halo, int* ctas_per_sm,
-                   size_t* smem_per_row);
+
+// Shared-memory attribute and occupancy for the resident kernel of this
+// lattice / threshold kind: blocks that fit on one SM (0 if none).
+int resident_prepare(const Geom& g, int thr_kind, int threads, size_t smem_bytes, int* blocks_per_sm);
+
+// ring: per-sweep hashes (nullptr = off; must be zeroed).  counts: density
+// counters sampled after every sweep s with s + 1 >= burn and
+// (s + 1 - burn) % stride == 0 (nullptr or stride 0 = off).
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
-                    unsigned int epoch, void* stream);
+                    unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
+                    uint32_t stride, void* stream);
 
 }  // namespace tl

@@ -14,326 +14,11 @@
 // word is updated with atomicXor.  The paper's second kernel (UpdateBlack /
 // UpdateWhite, which rebuilt the redundant 4-bit states of the other colour)
 // has no counterpart: the packed state stores every edge once.
-#include "tl_internal.h"
+#include "tl_device.cuh"
 
 #include <cstdint>
 
 namespace tl {
-
-#define TL_DEV __device__ __forceinline__
-
-// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
-// 32x32->64 multiplications by fixed odd constants, XOR of the high halves
-// into the other two words and the round key, and a Weyl key schedule.
-TL_DEV uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                      uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = c0 * 0xD2511F53u, hi0 = __umulhi(c0, 0xD2511F53u);
-        const uint32_t lo1 = c2 * 0xCD9E8D57u, hi1 = __umulhi(c2, 0xCD9E8D57u);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
-TL_DEV uint4 ld4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p); }
-TL_DEV void st4(uint32_t* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
-TL_DEV uint4 x4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
-TL_DEV bool any4(uint4 a) { return (a.x | a.y | a.z | a.w) != 0u; }
-
-// Site j of a plane shifted by one: bit j of the result is bit j-1 (shl) or
-// bit j+1 (shr) of the plane row, using the neighbouring words.
-TL_DEV uint4 shl1(uint4 w, uint32_t prev)
-{
-    return make_uint4((w.x << 1) | (prev >> 31), (w.y << 1) | (w.x >> 31),
-                      (w.z << 1) | (w.y >> 31), (w.w << 1) | (w.z >> 31));
-}
-TL_DEV uint4 shr1(uint4 w, uint32_t next)
-{
-    return make_uint4((w.x >> 1) | (w.y << 31), (w.y >> 1) | (w.z << 31),
-                      (w.z >> 1) | (w.w << 31), (w.w >> 1) | (next << 31));
-}
-
-// Apply flips to a plane whose bit j-1 belongs to site j.  Words k0..k0+2
-// belong to this group alone; word k0+3 shares its top bit with the next
-// group and word k0-1 its top bit with this one: those two use atomicXor.
-TL_DEV void store_shl(uint32_t* p, uint4 raw, uint4 fl, int k0)
-{
-    p[0] = raw.x ^ ((fl.x >> 1) | (fl.y << 31));
-    p[1] = raw.y ^ ((fl.y >> 1) | (fl.z << 31));
-    p[2] = raw.z ^ ((fl.z >> 1) | (fl.w << 31));
-    if (fl.w >> 1) atomicXor(p + 3, fl.w >> 1);
-    if ((fl.x & 1u) && k0 > 0) atomicXor(p - 1, 0x80000000u);
-}
-// Apply flips to a plane whose bit j+1 belongs to site j (mirror image).
-TL_DEV void store_shr(uint32_t* p, uint4 raw, uint4 fl, int k0, int K)
-{
-    if (fl.x << 1) atomicXor(p, fl.x << 1);
-    p[1] = raw.y ^ ((fl.y << 1) | (fl.x >> 31));
-    p[2] = raw.z ^ ((fl.z << 1) | (fl.y >> 31));
-    p[3] = raw.w ^ ((fl.w << 1) | (fl.z >> 31));
-    if ((fl.w >> 31) && k0 + 4 < K) atomicXor(p + 4, 1u);
-}
-
-// Heat-bath draw for the flippable sites f of one group: UP iff u < t.  The
-// comparison is exact and MSB first; plane k of u is one Philox output with
-// counter (group, sweep, (k << 16) | pass, stream).  It stops once no
-// flippable site is undecided, or after plane kmax, beyond which every
-// remaining threshold bit is zero (so an undecided u is >= t).
-template <class TB>
-TL_DEV uint4 heat_bath(uint4 f, uint32_t grp, uint32_t sweep, uint32_t pass, const DevRng& rng,
-                       int kmax, const TB& tb)
-{
-    uint4 und = f;
-    uint4 lt = make_uint4(0u, 0u, 0u, 0u);
-    for (int k = 0; k <= kmax; ++k) {
-        if (!any4(und)) break;
-        const uint4 o = philox10(grp, sweep, ((uint32_t)k << 16) | pass, rng.stream, rng.k0, rng.k1);
-        const uint4 t = tb(k);
-        uint32_t d;
-        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
-        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
-        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
-        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
-    }
-    return lt;
-}
-
-struct TbScalar {
-    uint32_t t;
-    TL_DEV uint4 operator()(int k) const
-    {
-        const uint32_t b = ((t >> (31 - k)) & 1u) ? 0xFFFFFFFFu : 0u;
-        return make_uint4(b, b, b, b);
-    }
-};
-struct TbPlanes {
-    const uint32_t* p;  // plane 0 of this group's four words
-    int K;
-    TL_DEV uint4 operator()(int k) const { return ld4(p + (size_t)k * K); }
-};
-
-// Bit-sliced 16-entry lookup: bit (31-k) of t16[idx] for each site, idx from
-// its four corner bits (idx bit 0 = tl, 1 = tr, 2 = br, 3 = bl).
-TL_DEV uint32_t sel_pair(uint32_t x, uint32_t tt, int q)
-{
-    const uint32_t a = (tt >> (2 * q)) & 1u, b = (tt >> (2 * q + 1)) & 1u;
-    return ((0u - a) & ~x) | ((0u - b) & x);
-}
-TL_DEV uint32_t lut16(uint32_t tl, uint32_t tr, uint32_t br, uint32_t bl, uint32_t tt)
-{
-    if (tt == 0u) return 0u;
-    if (tt == 0xFFFFu) return 0xFFFFFFFFu;
-    uint32_t v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = sel_pair(tl, tt, q);
-    uint32_t w[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) w[r] = (tr & v[2 * r + 1]) | (~tr & v[2 * r]);
-    const uint32_t z0 = (br & w[1]) | (~br & w[0]);
-    const uint32_t z1 = (br & w[3]) | (~br & w[2]);
-    return (bl & z1) | (~bl & z0);
-}
-struct TbTable {
-    const uint32_t* tmask;
-    uint4 tl, tr, br, bl;
-    TL_DEV uint4 operator()(int k) const
-    {
-        const uint32_t tt = tmask[k];
-        return make_uint4(lut16(tl.x, tr.x, br.x, bl.x, tt), lut16(tl.y, tr.y, br.y, bl.y, tt),
-                          lut16(tl.z, tr.z, br.z, bl.z, tt), lut16(tl.w, tr.w, br.w, bl.w, tt));
-    }
-};
-
-TL_DEV uint32_t range_mask(int k, int jlo, int jhi)
-{
-    int lo = jlo - 32 * k, hi = jhi - 32 * k;
-    if (hi < 0 || lo > 31 || lo > hi) return 0u;
-    lo = lo < 0 ? 0 : lo;
-    hi = hi > 31 ? 31 : hi;
-    const uint32_t mhi = (hi == 31) ? 0xFFFFFFFFu : ((1u << (hi + 1)) - 1u);
-    return mhi & ~((1u << lo) - 1u);
-}
-
-// ---------------------------------------------------------------------------
-// Dominoes (Sec. 1.1.3, Sec. 2.2).  Row y, class `pass`: sites x = 2j + p with
-// p = (pass + y) mod 2.  Edges: E = Hz(x,y), W = Hz(x-1,y), N = Vt(x,y),
-// S = Vt(x,y-1).  Planes 0 Hz_even, 1 Hz_odd, 2 Vt_even, 3 Vt_odd.
-// `row` points at plane 0 of row y; RW is the row pitch in words.
-// ---------------------------------------------------------------------------
-template <int TK>
-TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                          uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
-{
-    const int p = (int)((pass + (uint32_t)y) & 1u);
-    const int k0 = m << 2;
-    uint32_t* pE = row + (size_t)p * K + k0;
-    uint32_t* pN = row + (size_t)(2 + p) * K + k0;
-    uint32_t* pS = row - RW + (size_t)(2 + p) * K + k0;
-    uint32_t* pHe = row + k0;
-    uint32_t* pHo = row + (size_t)K + k0;
-    const uint4 E = ld4(pE), N = ld4(pN), S = ld4(pS);
-    uint4 Wd, Ho;
-    if (p) {
-        Wd = ld4(pHe);
-        Ho = Wd;
-    } else {
-        Ho = ld4(pHo);
-        Wd = shl1(Ho, k0 ? pHo[-1] : 0u);
-    }
-    uint4 f;
-    f.x = (E.x & Wd.x & ~(N.x | S.x)) | (N.x & S.x & ~(E.x | Wd.x));
-    f.y = (E.y & Wd.y & ~(N.y | S.y)) | (N.y & S.y & ~(E.y | Wd.y));
-    f.z = (E.z & Wd.z & ~(N.z | S.z)) | (N.z & S.z & ~(E.z | Wd.z));
-    f.w = (E.w & Wd.w & ~(N.w | S.w)) | (N.w & S.w & ~(E.w | Wd.w));
-    if (!any4(f)) return;
-    uint4 lt;
-    if (TK == THR_SITE) {
-        TbPlanes tb{th.planes + ((size_t)(y * 2 + p) * 32) * K + k0, K};
-        lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
-    } else {
-        TbScalar tb{th.scalar};
-        lt = heat_bath(f, grp, sweep, pass, rng, th.kmax, tb);
-    }
-    // a flippable site with E set is UP now; it flips iff the draw disagrees
-    const uint4 fl = make_uint4(f.x & (lt.x ^ E.x), f.y & (lt.y ^ E.y), f.z & (lt.z ^ E.z),
-                                f.w & (lt.w ^ E.w));
-    if (!any4(fl)) return;
-    st4(pE, x4(E, fl));
-    st4(pN, x4(N, fl));
-    st4(pS, x4(S, fl));
-    if (p) st4(pHe, x4(Wd, fl));
-    else store_shl(pHo, Ho, fl, k0);
-}
-
-// ---------------------------------------------------------------------------
-// Lozenges (Sec. 1.2.1).  Row y, class `pass`: sites x = 3j + r with
-// r = (pass - y) mod 3.  Six edges in angular order e0 = E1(x,y),
-// e1 = E3(x,y), e2 = E2(x,y), e3 = E1(x-1,y), e4 = E3(x-1,y-1),
-// e5 = E2(x,y-1); UP (cube present) = {e0,e2,e4}, DOWN = {e1,e3,e5}.
-// Planes: E1_r = r, E2_r = 3 + r, E3_r = 6 + r.
-// ---------------------------------------------------------------------------
-template <int TK>
-TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                           uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
-{
-    const int r = (int)((pass + 3u - (uint32_t)(y % 3)) % 3u);
-    const int k0 = m << 2;
-    uint32_t* dn = row - RW;
-    uint32_t* p0 = row + (size_t)r * K + k0;
-    uint32_t* p1 = row + (size_t)(6 + r) * K + k0;
-    uint32_t* p2 = row + (size_t)(3 + r) * K + k0;
-    uint32_t* p5 = dn + (size_t)(3 + r) * K + k0;
-    uint32_t *p3, *p4;
-    const uint4 e0 = ld4(p0), e1 = ld4(p1), e2 = ld4(p2), e5 = ld4(p5);
-    uint4 e3, e4, raw3, raw4;
-    if (r) {
-        p3 = row + (size_t)(r - 1) * K + k0;
-        p4 = dn + (size_t)(6 + r - 1) * K + k0;
-        e3 = raw3 = ld4(p3);
-        e4 = raw4 = ld4(p4);
-    } else {
-        p3 = row + (size_t)2 * K + k0;
-        p4 = dn + (size_t)8 * K + k0;
-        raw3 = ld4(p3);
-        raw4 = ld4(p4);
-        e3 = shl1(raw3, k0 ? p3[-1] : 0u);
-        e4 = shl1(raw4, k0 ? p4[-1] : 0u);
-    }
-    uint4 f;
-#define TL_LOZ_F(c) ((e0.c & e2.c & e4.c & ~(e1.c | e3.c | e5.c)) | (e1.c & e3.c & e5.c & ~(e0.c | e2.c | e4.c)))
-    f.x = TL_LOZ_F(x); f.y = TL_LOZ_F(y); f.z = TL_LOZ_F(z); f.w = TL_LOZ_F(w);
-#undef TL_LOZ_F
-    if (!any4(f)) return;
-    uint4 lt;
-    if (TK == THR_SITE) {
-        TbPlanes tb{th.planes + ((size_t)(y * 3 + r) * 32) * K + k0, K};
-        lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
-    } else {
-        TbScalar tb{th.scalar};
-        lt = heat_bath(f, grp, sweep, pass, rng, th.kmax, tb);
-    }
-    const uint4 fl = make_uint4(f.x & (lt.x ^ e0.x), f.y & (lt.y ^ e0.y), f.z & (lt.z ^ e0.z),
-                                f.w & (lt.w ^ e0.w));
-    if (!any4(fl)) return;
-    st4(p0, x4(e0, fl));
-    st4(p1, x4(e1, fl));
-    st4(p2, x4(e2, fl));
-    st4(p5, x4(e5, fl));
-    if (r) {
-        st4(p3, x4(raw3, fl));
-        st4(p4, x4(raw4, fl));
-    } else {
-        store_shl(p3, raw3, fl, k0);
-        store_shl(p4, raw4, fl, k0);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Six-vertex faces (Sec. 1.2.4, Fig. 5C).  Face row Y (vertex rows Y, Y+1),
-// class (px, py) from the pass order (0,0),(1,1),(1,0),(0,1): faces
-// X = 2j + px.  B = Hz(X,Y), T = Hz(X,Y+1), L = Vt(X,Y), R = Vt(X+1,Y);
-// corner bits TL = Vt(X,Y+1), TR = Hz(X+1,Y+1), BR = Hz(X+1,Y),
-// BL = Hz(X-1,Y).  UP = path through B and L.  Interior faces only.
-// ---------------------------------------------------------------------------
-TL_DEV int sixv_px(uint32_t pass) { return (pass == 1u || pass == 2u) ? 1 : 0; }
-TL_DEV int sixv_py(uint32_t pass) { return (pass == 1u || pass == 3u) ? 1 : 0; }
-
-TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, uint32_t pass,
-                        uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
-{
-    const int px = sixv_px(pass);
-    const int k0 = m << 2;
-    uint32_t* up = row + RW;
-    uint32_t *pB, *pT, *pL, *pR;
-    uint4 B, T, L, R, TL, TR, BR, BL, rawR;
-    if (px == 0) {
-        pB = row + k0;
-        pT = up + k0;
-        pL = row + (size_t)2 * K + k0;
-        pR = row + (size_t)3 * K + k0;
-        B = ld4(pB); T = ld4(pT); L = ld4(pL); R = rawR = ld4(pR);
-        BR = ld4(row + (size_t)K + k0);
-        TR = ld4(up + (size_t)K + k0);
-        TL = ld4(up + (size_t)2 * K + k0);
-        BL = shl1(BR, k0 ? row[(size_t)K + k0 - 1] : 0u);
-    } else {
-        pB = row + (size_t)K + k0;
-        pT = up + (size_t)K + k0;
-        pL = row + (size_t)3 * K + k0;
-        pR = row + (size_t)2 * K + k0;
-        B = ld4(pB); T = ld4(pT); L = ld4(pL);
-        TL = ld4(up + (size_t)3 * K + k0);
-        BL = ld4(row + k0);
-        const bool more = k0 + 4 < K;
-        BR = shr1(BL, more ? row[k0 + 4] : 0u);
-        TR = shr1(ld4(up + k0), more ? up[k0 + 4] : 0u);
-        rawR = ld4(pR);
-        R = shr1(rawR, more ? pR[4] : 0u);
-    }
-    const int jlo = px ? 0 : 1;
-    const int jhi = (N - 1 - px) >> 1;
-    uint4 f;
-#define TL_6V_F(c, i) (((B.c & L.c & ~(R.c | T.c)) | (R.c & T.c & ~(B.c | L.c))) & range_mask(k0 + i, jlo, jhi))
-    f.x = TL_6V_F(x, 0); f.y = TL_6V_F(y, 1); f.z = TL_6V_F(z, 2); f.w = TL_6V_F(w, 3);
-#undef TL_6V_F
-    if (!any4(f)) return;
-    TbTable tb{th.tmask, TL, TR, BR, BL};
-    const uint4 lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
-    const uint4 fl = make_uint4(f.x & (lt.x ^ B.x), f.y & (lt.y ^ B.y), f.z & (lt.z ^ B.z),
-                                f.w & (lt.w ^ B.w));
-    if (!any4(fl)) return;
-    st4(pB, x4(B, fl));
-    st4(pT, x4(T, fl));
-    st4(pL, x4(L, fl));
-    if (px == 0) st4(pR, x4(rawR, fl));
-    else store_shr(pR, rawR, fl, k0, K);
-}
 
 // ---------------------------------------------------------------------------
 // One launch per pass, state in global memory (L2-resident for mid sizes).
@@ -364,9 +49,7 @@ __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__
     if (m < gr.x || m >= gr.y) return;
     const uint32_t grp = (uint32_t)(rr * g.Kg + m);
     uint32_t* row = rows0 + (int64_t)y * g.row_words;
-    if (LAT == LAT_DOMINO) domino_update<TK>(row, g.row_words, g.K, y, m, pass, grp, sweep, rng, th);
-    else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, g.row_words, g.K, y, m, pass, grp, sweep, rng, th);
-    else sixv_update(row, g.row_words, g.K, g.N, y, m, pass, grp, sweep, rng, th);
+    group_update<LAT, TK>(row, g.row_words, g, y, m, pass, grp, sweep, rng, th);
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -491,34 +174,18 @@ int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t*
 // ---------------------------------------------------------------------------
 // Observables.
 // ---------------------------------------------------------------------------
-// splitmix64 output for state x (Steele, Lea & Flood 2014).
-TL_DEV uint64_t mix64(uint64_t x)
-{
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 __global__ void hash_kernel(const uint32_t* __restrict__ rows0, Geom g, unsigned long long* out)
 {
     const int64_t n = (int64_t)g.H * g.row_words;
     uint64_t acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t w = rows0[i];
+        const uint32_t w = rows0[i];
         if (!w) continue;
         const int y = (int)(i / g.row_words);
         const int rem = (int)(i - (int64_t)y * g.row_words);
         const int pl = rem / g.K, k = rem - pl * g.K;
-        const int type = pl / g.npar, res = pl - type * g.npar;
-        const uint64_t base = ((uint64_t)type * g.H + y) * (uint64_t)g.W;
-        while (w) {
-            const int b = __ffs(w) - 1;
-            w &= w - 1;
-            const int x = g.npar * (32 * k + b) + res;
-            if (x < g.W) acc += mix64(base + (uint64_t)x);
-        }
+        acc += word_hash(w, g, y, pl, k);
     }
     for (int off = 16; off; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (unsigned long long)acc);
@@ -539,19 +206,12 @@ __global__ void density_acc_kernel(const uint32_t* __restrict__ rows0, Geom g, u
     const int64_t n = (int64_t)g.H * g.row_words;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t w = rows0[i];
+        const uint32_t w = rows0[i];
         if (!w) continue;
         const int y = (int)(i / g.row_words);
         const int rem = (int)(i - (int64_t)y * g.row_words);
         const int pl = rem / g.K, k = rem - pl * g.K;
-        const int type = pl / g.npar, res = pl - type * g.npar;
-        uint32_t* c = counts + ((size_t)type * g.H + y) * g.W;
-        while (w) {
-            const int b = __ffs(w) - 1;
-            w &= w - 1;
-            const int x = g.npar * (32 * k + b) + res;
-            if (x < g.W) c[x] += 1u;
-        }
+        word_count(w, g, y, pl, k, counts);
     }
 }
 

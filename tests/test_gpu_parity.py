@@ -47,7 +47,7 @@ def _lat(kind):
     return {"aztec": O.DOMINO, "rect": O.DOMINO, "hex": O.LOZENGE, "dwbc": O.SIXV}[kind]
 
 
-def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, scalar=None,
+def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, halo=0, scalar=None,
               site=None, w6=None, hashed=True):
     dom = _domain(T, kind, args)
     lat = _lat(kind)
@@ -62,8 +62,8 @@ def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, scalar=
         th = T.thresholds(scalar=scalar)
         okw = dict(t_scalar=scalar)
     ch = T.Chain(ctx, dom, seed=seed, stream_id=stream, th=th)
-    if kernel or spl:
-        ch.set_plan(kernel, spl)
+    if kernel or spl or halo:
+        ch.set_plan(kernel, spl, halo)
     st = _oracle_state(kind, args)
     if hashed:
         ring = ch.run_hashed(k)
@@ -73,6 +73,7 @@ def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, scalar=
     else:
         ch.run(k)
         O.sweeps(lat, st, seed=seed, stream=stream, k=k, **okw)
+    ch.sync()
     got = ch.read_state()
     assert np.array_equal(got, st)
     assert ch.state_hash() == O.state_hash(st)
@@ -90,7 +91,7 @@ def test_aztec32_uniform_every_sweep_full_length(T, ctx):
 
 @pytest.mark.parametrize("kind,args", [
     ("aztec", (1,)), ("aztec", (2,)), ("aztec", (63,)), ("aztec", (64,)), ("aztec", (129,)),
-    ("rect", (2, 2)), ("rect", (300, 7)), ("rect", (255, 9)), ("rect", (7, 40)),
+    ("rect", (2, 2)), ("rect", (300, 7)), ("rect", (255, 8)), ("rect", (7, 40)),
 ])
 def test_domino_uniform_sizes(T, ctx, kind, args):
     _run_pair(T, ctx, kind, args, seed=12345, stream=3, k=60, scalar=1 << 31)
@@ -133,6 +134,50 @@ def test_sixv_dwbc_sqrt2(T, ctx, N):
                                 [0.7, 1.3, 0.4, 1.9, 1.1, 0.6]])
 def test_sixv_weights(T, ctx, w6):
     _run_pair(T, ctx, "dwbc", (130,), seed=2, stream=9, k=40, w6=w6)
+
+
+# ---------------------------------------------------------------------------
+# Both kernel families, several halo depths and launch splits
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,args", [("aztec", (70,)), ("hex", (40, 50, 45)), ("dwbc", (120,))])
+def test_global_per_pass_kernel(T, ctx, kind, args):
+    kw = dict(w6=SQ2) if kind == "dwbc" else dict(scalar=(1 << 31) if kind == "aztec" else 0x7FF80000)
+    _run_pair(T, ctx, kind, args, seed=17, k=30, kernel=1, **kw)
+
+
+@pytest.mark.parametrize("halo", [1, 2, 3, 5, 8, 13])
+@pytest.mark.parametrize("kind,args", [("aztec", (90,)), ("hex", (60, 70, 50)), ("dwbc", (150,))])
+def test_resident_kernel_halos(T, ctx, kind, args, halo):
+    kw = dict(w6=SQ2) if kind == "dwbc" else dict(scalar=(1 << 31) if kind == "aztec" else 0x7FF80000)
+    _run_pair(T, ctx, kind, args, seed=23, k=25, kernel=2, halo=halo, **kw)
+
+
+@pytest.mark.parametrize("spl", [1, 4, 7])
+def test_resident_kernel_launch_splits(T, ctx, spl):
+    _run_pair(T, ctx, "aztec", (128,), seed=31, k=30, kernel=2, spl=spl, scalar=1 << 31)
+
+
+def test_resident_weighted(T, ctx):
+    n = 150
+    rng = np.random.default_rng(1)
+    w = np.exp(0.5 * rng.standard_normal((2, 2 * n + 1, 2 * n + 1)))
+    _run_pair(T, ctx, "aztec", (n,), seed=3, stream=77, k=30, kernel=2, site=O.domino_thresholds(w))
+
+
+def test_resident_density_matches_global(T, ctx):
+    dom = T.Domain.aztec(100)
+    out = []
+    for kernel in (1, 2):
+        ch = T.Chain(ctx, dom, seed=12, th=T.thresholds(scalar=1 << 31))
+        ch.set_plan(kernel)
+        ch.density_begin(stride=7, burn_in=20)
+        ch.run(33)
+        ch.run(60)
+        ch.sync()
+        d, n = ch.read_density()
+        out.append((d, n, ch.state_hash()))
+    assert out[0][1] == out[1][1] == (93 - 20) // 7 + 1
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][2] == out[1][2]
 
 
 def test_results_do_not_depend_on_how_sweeps_are_split(T, ctx):
