@@ -270,13 +270,29 @@ int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* samples, voi
  * (so the all-horizontal start is north in the upper half) and 0 otherwise. */
 int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream);
 
-/* Launch-planner controls (for tests and tuning).  kernel: 0 automatic, 1
- * the one-launch-per-pass global-memory kernel, 2 the shared-memory resident
- * multi-sweep kernel (TL_EUNSUPPORTED if the domain does not fit it).
- * sweeps_per_launch: cap on sweeps per resident launch (0 = no cap).  halo:
- * passes between boundary exchanges of the resident kernel (0 = automatic,
- * at most 64).  Results do not depend on any of them. */
-int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch, int halo);
+/* Launch plan of a chain.  Every field 0 means "automatic".  Results never
+ * depend on the plan: the random numbers are keyed by site and sweep.
+ *  kernel:            1 one launch per pass over global memory; 2 the
+ *                     shared-memory resident multi-sweep kernel (cooperative
+ *                     launch; TL_EUNSUPPORTED if the domain does not fit it).
+ *  sweeps_per_launch: cap on sweeps per resident launch.
+ *  halo:              passes between boundary exchanges of the resident
+ *                     kernel (1..64).
+ *  threads:           threads per CTA of the resident kernel (512 or 1024).
+ *  npre:              random bit planes generated ahead per group (1..4).
+ * tl_chain_get_plan also fills the resolved values and ctas / smem_bytes. */
+typedef struct {
+    int kernel;
+    int sweeps_per_launch;
+    int halo;
+    int threads;
+    int npre;
+    int ctas;            /* out: CTAs of the resident kernel (0 if not used) */
+    int smem_bytes;      /* out: dynamic shared memory per CTA */
+} tl_plan;
+
+int tl_chain_set_plan(tl_chain* c, const tl_plan* plan);
+int tl_chain_get_plan(tl_chain* c, tl_plan* plan);
 
 /* Wait for the chain's work on `stream` and report a failure of the
  * resident kernel's bounded waits (TL_ETIMEOUT; the state is then

@@ -50,6 +50,15 @@ class DomainInfo(ctypes.Structure):
                 ("height_height", ctypes.c_int)]
 
 
+class Plan(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("sweeps_per_launch", ctypes.c_int),
+                ("halo", ctypes.c_int), ("threads", ctypes.c_int), ("npre", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("smem_bytes", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Thresholds(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("scalar", ctypes.c_uint32),
                 ("site", ctypes.c_void_p), ("table16", ctypes.c_uint32 * 16)]
@@ -77,7 +86,8 @@ _SIG = {
     "tl_chain_reset": (_i, [_vp, _vp]),
     "tl_chain_sweep": (_u64, [_vp]),
     "tl_chain_launches": (_u64, [_vp]),
-    "tl_chain_set_plan": (_i, [_vp, _i, _i, _i]),
+    "tl_chain_set_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
+    "tl_chain_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_sync": (_i, [_vp, _vp]),
     "tl_run_sweeps": (_i, [_vp, _u64, _vp]),
     "tl_run_sweeps_hashed": (_i, [_vp, _u64, _vp, _vp]),
@@ -263,9 +273,16 @@ class Chain:
     def reset(self, stream=None):
         _check(_lib.tl_chain_reset(self._h, _stream(stream)))
 
-    def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0):
+    def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0,
+                 threads: int = 0, npre: int = 0):
         """kernel 0 auto / 1 per-pass global / 2 resident; results never depend on it."""
-        _check(_lib.tl_chain_set_plan(self._h, kernel, sweeps_per_launch, halo))
+        p = Plan(kernel, sweeps_per_launch, halo, threads, npre, 0, 0)
+        _check(_lib.tl_chain_set_plan(self._h, ctypes.byref(p)))
+
+    def plan(self) -> dict:
+        p = Plan()
+        _check(_lib.tl_chain_get_plan(self._h, ctypes.byref(p)))
+        return p.as_dict()
 
     def sync(self, stream=None):
         _check(_lib.tl_chain_sync(self._h, _stream(stream)))

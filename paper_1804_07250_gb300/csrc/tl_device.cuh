@@ -71,18 +71,17 @@ TL_DEV void store_shr(uint32_t* p, uint4 raw, uint4 fl, int k0, int K)
 
 // Heat-bath draw for the flippable sites f of one group: UP iff u < t.  The
 // comparison is exact and MSB first; plane k of u is one Philox output with
-// counter (group, sweep, (k << 16) | pass, stream).  It stops once no
-// flippable site is undecided, or after plane kmax, beyond which every
-// remaining threshold bit is zero (so an undecided u is >= t).
-template <class TB>
-TL_DEV uint4 heat_bath(uint4 f, uint32_t grp, uint32_t sweep, uint32_t pass, const DevRng& rng,
-                       int kmax, const TB& tb)
+// counter (group, sweep, (k << 16) | pass, stream), supplied by `rnd`.  It
+// stops once no flippable site is undecided, or after plane kmax, beyond
+// which every remaining threshold bit is zero (so an undecided u is >= t).
+template <class RND, class TB>
+TL_DEV uint4 heat_bath(uint4 f, int kmax, const RND& rnd, const TB& tb)
 {
     uint4 und = f;
     uint4 lt = make_uint4(0u, 0u, 0u, 0u);
     for (int k = 0; k <= kmax; ++k) {
         if (!any4(und)) break;
-        const uint4 o = philox10(grp, sweep, ((uint32_t)k << 16) | pass, rng.stream, rng.k0, rng.k1);
+        const uint4 o = rnd(k);
         const uint4 t = tb(k);
         uint32_t d;
         d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
@@ -92,6 +91,24 @@ TL_DEV uint4 heat_bath(uint4 f, uint32_t grp, uint32_t sweep, uint32_t pass, con
     }
     return lt;
 }
+
+// Random planes computed on the spot.
+struct RndPhilox {
+    uint32_t grp, sweep, pass;
+    DevRng rng;
+    TL_DEV uint4 operator()(int k) const
+    {
+        return philox10(grp, sweep, ((uint32_t)k << 16) | pass, rng.stream, rng.k0, rng.k1);
+    }
+};
+// The first `npre` planes precomputed (shared memory, plane-major with
+// stride `stride` uint4s), the rest computed on the spot.
+struct RndPre {
+    const uint4* pre;
+    int npre, stride;
+    RndPhilox more;
+    TL_DEV uint4 operator()(int k) const { return k < npre ? pre[(size_t)k * stride] : more(k); }
+};
 
 struct TbScalar {
     uint32_t t;
@@ -155,9 +172,9 @@ TL_DEV uint32_t range_mask(int k, int jlo, int jhi)
 // S = Vt(x,y-1).  Planes 0 Hz_even, 1 Hz_odd, 2 Vt_even, 3 Vt_odd.
 // `row` points at plane 0 of row y; RW is the row pitch in words.
 // ---------------------------------------------------------------------------
-template <int TK>
+template <int TK, class RND>
 TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                          uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
+                          const RND& rnd, const ThrView& th)
 {
     const int p = (int)((pass + (uint32_t)y) & 1u);
     const int k0 = m << 2;
@@ -184,10 +201,10 @@ TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32
     uint4 lt;
     if (TK == THR_SITE) {
         TbPlanes tb{th.planes + ((size_t)(y * 2 + p) * 32) * K + k0, K};
-        lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
+        lt = heat_bath(f, 31, rnd, tb);
     } else {
         TbScalar tb{th.scalar};
-        lt = heat_bath(f, grp, sweep, pass, rng, th.kmax, tb);
+        lt = heat_bath(f, th.kmax, rnd, tb);
     }
     // a flippable site with E set is UP now; it flips iff the draw disagrees
     const uint4 fl = make_uint4(f.x & (lt.x ^ E.x), f.y & (lt.y ^ E.y), f.z & (lt.z ^ E.z),
@@ -207,9 +224,9 @@ TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32
 // e5 = E2(x,y-1); UP (cube present) = {e0,e2,e4}, DOWN = {e1,e3,e5}.
 // Planes: E1_r = r, E2_r = 3 + r, E3_r = 6 + r.
 // ---------------------------------------------------------------------------
-template <int TK>
+template <int TK, class RND>
 TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                           uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
+                           const RND& rnd, const ThrView& th)
 {
     const int r = (int)((pass + 3u - (uint32_t)(y % 3)) % 3u);
     const int k0 = m << 2;
@@ -242,10 +259,10 @@ TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint3
     uint4 lt;
     if (TK == THR_SITE) {
         TbPlanes tb{th.planes + ((size_t)(y * 3 + r) * 32) * K + k0, K};
-        lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
+        lt = heat_bath(f, 31, rnd, tb);
     } else {
         TbScalar tb{th.scalar};
-        lt = heat_bath(f, grp, sweep, pass, rng, th.kmax, tb);
+        lt = heat_bath(f, th.kmax, rnd, tb);
     }
     const uint4 fl = make_uint4(f.x & (lt.x ^ e0.x), f.y & (lt.y ^ e0.y), f.z & (lt.z ^ e0.z),
                                 f.w & (lt.w ^ e0.w));
@@ -273,8 +290,9 @@ TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint3
 TL_DEV int sixv_px(uint32_t pass) { return (pass == 1u || pass == 2u) ? 1 : 0; }
 TL_DEV int sixv_py(uint32_t pass) { return (pass == 1u || pass == 3u) ? 1 : 0; }
 
+template <class RND>
 TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, uint32_t pass,
-                        uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
+                        const RND& rnd, const ThrView& th)
 {
     const int px = sixv_px(pass);
     const int k0 = m << 2;
@@ -313,7 +331,7 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
 #undef TL_6V_F
     if (!any4(f)) return;
     TbTable tb{th.tmask, TL, TR, BR, BL};
-    const uint4 lt = heat_bath(f, grp, sweep, pass, rng, 31, tb);
+    const uint4 lt = heat_bath(f, 31, rnd, tb);
     const uint4 fl = make_uint4(f.x & (lt.x ^ B.x), f.y & (lt.y ^ B.y), f.z & (lt.z ^ B.z),
                                 f.w & (lt.w ^ B.w));
     if (!any4(fl)) return;
@@ -326,13 +344,13 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
 
 
 // Dispatch one group update for lattice LAT.
-template <int LAT, int TK>
+template <int LAT, int TK, class RND>
 TL_DEV void group_update(uint32_t* row, int64_t RW, const Geom& g, int y, int m, uint32_t pass,
-                         uint32_t grp, uint32_t sweep, const DevRng& rng, const ThrView& th)
+                         const RND& rnd, const ThrView& th)
 {
-    if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, grp, sweep, rng, th);
-    else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, grp, sweep, rng, th);
-    else sixv_update(row, RW, g.K, g.N, y, m, pass, grp, sweep, rng, th);
+    if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
+    else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
+    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th);
 }
 
 // splitmix64 output for state x (Steele, Lea & Flood 2014).

@@ -583,9 +583,9 @@ struct tl_chain {
     bool res_ready = false, res_failed = false;
     ResidentPlan res{};
     int* stripe_d = nullptr;
-    uint32_t* xbuf_d = nullptr;
-    unsigned long long* flags_d = nullptr;
+    unsigned long long* xbuf_d = nullptr;
     int* status_d = nullptr;
+    int threads_req = 0, npre_req = 0;
     unsigned int epoch = 0;
     std::string res_why;
 };
@@ -607,7 +607,6 @@ static void chain_free(tl_chain* c)
     cudaFree(c->hscratch);
     cudaFree(c->stripe_d);
     cudaFree(c->xbuf_d);
-    cudaFree(c->flags_d);
     cudaFree(c->status_d);
     delete c;
 }
@@ -768,28 +767,45 @@ TL_API uint64_t tl_chain_launches(const tl_chain* c) { return c ? c->launches : 
 
 static bool want_resident(tl_chain* c);
 
-TL_API int tl_chain_set_plan(tl_chain* c, int kernel, int sweeps_per_launch, int halo)
+TL_API int tl_chain_set_plan(tl_chain* c, const tl_plan* p)
 {
-    if (!c || kernel < 0 || kernel > 2 || sweeps_per_launch < 0 || halo < 0 || halo > 64)
-        return fail(TL_EINVAL, "tl_chain_set_plan: bad argument");
+    if (!c || !p || p->kernel < 0 || p->kernel > 2 || p->sweeps_per_launch < 0 || p->halo < 0 ||
+        p->halo > 64 || (p->threads != 0 && p->threads != 512 && p->threads != 1024) || p->npre < 0 ||
+        p->npre > 4)
+        return fail(TL_EINVAL, "tl_chain_set_plan: bad plan");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
-    c->kernel = kernel;
-    c->spl = sweeps_per_launch;
-    if (halo != c->halo_req) {
+    c->kernel = p->kernel;
+    c->spl = p->sweeps_per_launch;
+    if (p->halo != c->halo_req || p->threads != c->threads_req || p->npre != c->npre_req) {
         CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(c->stripe_d);
         cudaFree(c->xbuf_d);
-        cudaFree(c->flags_d);
         cudaFree(c->status_d);
         c->stripe_d = nullptr;
         c->xbuf_d = nullptr;
-        c->flags_d = nullptr;
         c->status_d = nullptr;
         c->res_ready = c->res_failed = false;
-        c->halo_req = halo;
+        c->halo_req = p->halo;
+        c->threads_req = p->threads;
+        c->npre_req = p->npre;
     }
-    if (kernel == 2 && !want_resident(c))
+    if (p->kernel == 2 && !want_resident(c))
         return fail(TL_EUNSUPPORTED, "resident kernel unavailable: %s", c->res_why.c_str());
+    return TL_OK;
+}
+
+TL_API int tl_chain_get_plan(tl_chain* c, tl_plan* p)
+{
+    if (!c || !p) return fail(TL_EINVAL, "tl_chain_get_plan: NULL argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    const bool res = want_resident(c);
+    p->kernel = res ? 2 : 1;
+    p->sweeps_per_launch = c->spl;
+    p->halo = res ? c->res.halo : 0;
+    p->threads = res ? c->res.threads : 256;
+    p->npre = res ? c->res.npre : 0;
+    p->ctas = res ? c->res.ctas : 0;
+    p->smem_bytes = res ? (int)c->res.smem_bytes : 0;
     return TL_OK;
 }
 
@@ -833,10 +849,23 @@ static int take_sample(tl_chain* c, void* stream)
     return TL_OK;
 }
 
-// Default halo depth (passes per exchange) of the resident kernel.
+// Default halo depth (passes per exchange), threads per CTA and random
+// planes generated ahead for the resident kernel.
 static int default_halo(const Geom& g)
 {
     return g.lattice == LAT_DOMINO ? 8 : (g.lattice == LAT_LOZENGE ? 6 : 8);
+}
+static int default_npre(const tl_chain* c)
+{
+    if (c->th.kind == THR_SCALAR) return c->th.kmax < 0 ? 1 : std::min(4, c->th.kmax + 1);
+    return c->g.lattice == LAT_DOMINO ? 2 : 4;
+}
+
+// Local rows of stripe [lo, hi) of `C`, with halo h, clamped to the pads.
+static void stripe_local(int lo, int hi, int k, int C, int h, int H, int* slo, int* shi)
+{
+    *slo = k == 0 ? -1 : lo - h;
+    *shi = k == C - 1 ? H + 1 : hi + h;
 }
 
 // Stripe partition, shared-memory budget and buffers of the resident kernel.
@@ -845,24 +874,40 @@ static int plan_resident(tl_chain* c)
     const Geom& g = c->g;
     const tl_domain& d = c->dom_copy;
     const int h = c->halo_req > 0 ? c->halo_req : default_halo(g);
-    const int threads = 512;
-    // weight of a row: its active groups plus a fixed cost per row
+    const int threads = c->threads_req > 0 ? c->threads_req : (g.lattice == LAT_DOMINO ? 1024 : 512);
+    const int npre = c->npre_req > 0 ? c->npre_req : default_npre(c);
+    const bool sixv = g.lattice == LAT_SIXV;
+    std::vector<int> act(g.H, 0);
     std::vector<double> w(g.H, 0.0);
     double total = 0;
     for (int y = 0; y < g.H; ++y) {
         const int2 r = d.grange[y];
-        w[y] = 0.25 + std::max(0, r.y - r.x);
+        act[y] = std::max(0, r.y - r.x);
+        w[y] = 0.1 + act[y];
         total += w[y];
     }
+    // items of rows [a, b) (optionally one parity)
+    std::vector<int> pre(g.H + 1, 0), pre_par[2] = {std::vector<int>(g.H + 1, 0), std::vector<int>(g.H + 1, 0)};
+    for (int y = 0; y < g.H; ++y) {
+        pre[y + 1] = pre[y] + act[y];
+        for (int p = 0; p < 2; ++p) pre_par[p][y + 1] = pre_par[p][y] + ((y & 1) == p ? act[y] : 0);
+    }
+    auto items_in = [&](int a, int b, int par) {
+        a = std::max(a, 0);
+        b = std::min(b, g.H);
+        if (b <= a) return 0;
+        return par < 0 ? pre[b] - pre[a] : pre_par[par][b] - pre_par[par][a];
+    };
     int C = std::min(c->ctx->sms, g.H / h);
     if (C < 2) {
         c->res_why = "domain too small for stripes";
         return TL_EUNSUPPORTED;
     }
+    const size_t row_bytes = (size_t)g.row_words * 4;
     for (;;) {
         std::vector<int> lo(C + 1, 0);
-        double acc = 0;
         int y = 0;
+        double acc = 0;
         for (int k = 1; k < C; ++k) {
             const double target = total * k / C;
             const int ymin = lo[k - 1] + h;
@@ -874,9 +919,28 @@ static int plan_resident(tl_chain* c)
             lo[k] = y;
         }
         lo[C] = g.H;
-        int maxrows = 0;
-        for (int k = 0; k < C; ++k) maxrows = std::max(maxrows, lo[k + 1] - lo[k]);
-        const size_t smem = (size_t)(maxrows + 2 * h + 2) * (size_t)g.row_words * 4;
+        int max_nloc = 0, cap_items = 0, cap_cycle = 0;
+        for (int k = 0; k < C; ++k) {
+            int slo, shi;
+            stripe_local(lo[k], lo[k + 1], k, C, h, g.H, &slo, &shi);
+            max_nloc = std::max(max_nloc, shi - slo);
+            cap_items = std::max(cap_items, items_in(slo, shi, -1));
+            int cyc = 0;
+            for (int i = 1; i <= h; ++i) {
+                const int vlo = k == 0 ? -1 : slo + (i - 1);
+                const int vhi = k == C - 1 ? g.H + 1 : shi - (i - 1);
+                if (sixv) {
+                    const int a = std::max(vlo, 1), last = std::min(vhi - 2, g.N - 1);
+                    cyc += std::max(items_in(a, last + 1, 0), items_in(a, last + 1, 1));
+                } else {
+                    cyc += items_in(vlo + 1, vhi, -1);
+                }
+            }
+            cap_cycle = std::max(cap_cycle, cyc);
+        }
+        const int ntab = sixv ? 2 : 1;
+        const size_t smem = (size_t)max_nloc * row_bytes + (size_t)npre * cap_cycle * 16 + (size_t)cap_items * 4 +
+                            (size_t)ntab * (max_nloc + 1) * 4 + 16;
         if ((long)smem > (long)c->ctx->smem_optin) {
             c->res_why = "stripe does not fit in shared memory";
             return TL_EUNSUPPORTED;
@@ -893,18 +957,20 @@ static int plan_resident(tl_chain* c)
         int rc;
         if ((rc = dev_alloc(&c->stripe_d, (size_t)C + 1, "stripes")) ||
             (rc = dev_alloc(&c->xbuf_d, (size_t)C * 4 * h * g.row_words, "exchange buffer")) ||
-            (rc = dev_alloc(&c->flags_d, (size_t)C, "flags")) || (rc = dev_alloc(&c->status_d, 1, "status")))
+            (rc = dev_alloc(&c->status_d, 1, "status")))
             return rc;
         CUDA_TRY(cudaMemcpy(c->stripe_d, lo.data(), sizeof(int) * (C + 1), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemset(c->flags_d, 0, sizeof(unsigned long long) * C));
+        CUDA_TRY(cudaMemset(c->xbuf_d, 0, sizeof(unsigned long long) * C * 4 * h * g.row_words));
         CUDA_TRY(cudaMemset(c->status_d, 0, sizeof(int)));
         c->res.ctas = C;
         c->res.threads = threads;
         c->res.halo = h;
+        c->res.npre = npre;
+        c->res.cap_items = cap_items;
+        c->res.cap_cycle = cap_cycle;
         c->res.smem_bytes = smem;
         c->res.stripe_lo = c->stripe_d;
         c->res.xbuf = c->xbuf_d;
-        c->res.flags = c->flags_d;
         c->res.status = c->status_d;
         c->res_ready = true;
         return TL_OK;
@@ -923,10 +989,17 @@ static bool want_resident(tl_chain* c)
 // Resident launches over [c->sweep, c->sweep + k), at most spl sweeps each.
 static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void* stream)
 {
+    // exchange tags carry 16 bits of cycle and 16 bits of launch epoch
+    const uint64_t max_sweeps = std::max<uint64_t>(1, 60000ull * c->res.halo / c->g.passes);
     uint64_t done = 0;
     while (done < k) {
-        const uint64_t n = c->spl > 0 ? std::min<uint64_t>((uint64_t)c->spl, k - done) : k - done;
+        uint64_t n = c->spl > 0 ? std::min<uint64_t>((uint64_t)c->spl, k - done) : k - done;
+        n = std::min(n, max_sweeps);
         const bool dens = c->density_on;
+        if (((c->epoch + 1) & 0xFFFFu) == 0) {
+            const size_t nx = (size_t)c->res.ctas * 4 * c->res.halo * c->g.row_words;
+            CUDA_TRY(cudaMemsetAsync(c->xbuf_d, 0, nx * sizeof(unsigned long long), SS(stream)));
+        }
         const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
                                       c->grange, ++c->epoch, ring ? ring + done : nullptr,
                                       dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, stream);

@@ -85,12 +85,14 @@ int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t*
 // are recomputed redundantly, the valid region shrinking by one row per pass.
 struct ResidentPlan {
     int ctas;                      // cooperative grid size
-    int threads;                   // threads per CTA
+    int threads;                   // threads per CTA (512 or 1024)
     int halo;                      // passes per exchange cycle (= halo rows per side)
+    int npre;                      // random planes generated ahead per group
+    int cap_items;                 // item-table capacity per CTA
+    int cap_cycle;                 // groups touched per cycle, per CTA (upper bound)
     size_t smem_bytes;             // dynamic shared memory per CTA
     const int* stripe_lo;          // device [ctas + 1]
-    uint32_t* xbuf;                // device [ctas][2][2][halo][row_words]
-    unsigned long long* flags;     // device [ctas] progress flags (epoch << 32 | cycle)
+    unsigned long long* xbuf;      // device [ctas][2][2][halo][row_words] tagged words
     int* status;                   // device error word: 0 ok, 1 a bounded wait gave up
 };
 

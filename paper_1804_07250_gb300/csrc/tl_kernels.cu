@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__
     if (m < gr.x || m >= gr.y) return;
     const uint32_t grp = (uint32_t)(rr * g.Kg + m);
     uint32_t* row = rows0 + (int64_t)y * g.row_words;
-    group_update<LAT, TK>(row, g.row_words, g, y, m, pass, grp, sweep, rng, th);
+    const RndPhilox rnd{grp, sweep, pass, rng};
+    group_update<LAT, TK>(row, g.row_words, g, y, m, pass, rnd, th);
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }

@@ -7,10 +7,24 @@
 // row whose inputs are still exact; because a site only reads edges within
 // one row of it, the exact region shrinks by one row at each interior stripe
 // edge per pass, so after `halo` passes the CTA still holds its own rows
-// exactly.  It then publishes its top and bottom `halo` rows, waits for its
-// two neighbours' progress flags (bounded wait), and refreshes its halos.
-// State thus crosses the memory system once per `halo` passes and only at
-// stripe seams; the rest of the time it stays on chip.
+// exactly.  It then publishes its top and bottom `halo` rows and refreshes its
+// halos from its two neighbours.  State crosses the memory system once per
+// `halo` passes and only at stripe seams; otherwise it stays on chip.
+//
+// Within a cycle of `halo` passes the work is split in two phases:
+//  1. random planes: the first `npre` Philox planes of every group the cycle
+//     will touch are generated up front into shared memory -- independent
+//     work that keeps the integer pipes busy;
+//  2. passes: each active 128-site group (from a per-CTA item table that
+//     lists only groups holding domain sites) reads its planes from shared
+//     memory, so a pass is a short chain of shared-memory loads and bitwise
+//     logic; planes beyond `npre` are generated on the spot when needed.
+//
+// Exchange: every boundary word travels with a 32-bit tag (launch epoch,
+// cycle) in one 64-bit store; the reader polls the 64-bit words until the
+// tags match, so no separate fence or flag round trip is needed.  Buffers are
+// double-buffered by cycle parity.  Every wait is bounded (2 s); on expiry the
+// CTA raises the status word and returns.
 #include "tl_device.cuh"
 
 #include <cstdint>
@@ -21,13 +35,14 @@ struct ResParams {
     uint32_t* rows0;            // global row 0 (after the pad row)
     Geom g;
     const int* stripe_lo;
-    int halo;
+    int halo, npre;
+    int cap_items;              // item-table capacity per CTA
+    int cap_cycle;              // random-plane buffer capacity (groups per cycle)
     uint32_t sweep0, nsweeps;
     DevRng rng;
     ThrView th;
     const int2* grange;
-    uint32_t* xbuf;
-    unsigned long long* flags;
+    unsigned long long* xbuf;   // tagged exchange words
     int* status;
     unsigned long long* ring;
     uint32_t* counts;
@@ -36,26 +51,25 @@ struct ResParams {
     unsigned int epoch;
 };
 
-TL_DEV unsigned long long ld_acquire(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-TL_DEV void st_release(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 TL_DEV uint64_t globaltimer()
 {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+TL_DEV unsigned long long ld_relaxed(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+TL_DEV void st_relaxed(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far beyond any healthy exchange
 
-// Copy `nrows` packed rows (16-byte granules), L2 only on the global side.
 TL_DEV void copy_rows_to_global(uint32_t* dst, const uint32_t* src, int64_t words, int tid, int nt)
 {
     uint4* d = reinterpret_cast<uint4*>(dst);
@@ -69,66 +83,150 @@ TL_DEV void copy_rows_from_global(uint32_t* dst, const uint32_t* src, int64_t wo
     for (int64_t i = tid; i < words / 4; i += nt) d[i] = __ldcg(s + i);
 }
 
-template <int LAT, int TK>
-__global__ void __launch_bounds__(512, 1) resident_kernel(const ResParams P)
+// Item range of pass i (1-based) of a cycle: table `tab` entries [s, e).
+struct PassRange {
+    int tab, s, e;
+};
+
+template <int LAT>
+TL_DEV PassRange pass_range(const Geom& g, int i, uint32_t pass, int slo, int shi, bool bot, bool top,
+                            const int* off, int nloc)
+{
+    const int vlo = bot ? -1 : slo + (i - 1);
+    const int vhi = top ? g.H + 1 : shi - (i - 1);
+    PassRange r;
+    if (LAT == LAT_SIXV) {
+        // face rows Y in [max(vlo,1), min(vhi-2, N-1)] of the class parity
+        const int a = vlo > 1 ? vlo : 1;
+        const int last = (vhi - 2) < (g.N - 1) ? (vhi - 2) : (g.N - 1);
+        r.tab = sixv_py(pass);
+        if (last < a) {
+            r.s = r.e = 0;
+            return r;
+        }
+        const int* o = off + r.tab * (nloc + 1);
+        r.s = o[a - slo];
+        r.e = o[last + 1 - slo];
+    } else {
+        const int a = (vlo + 1) > 0 ? (vlo + 1) : 0;
+        const int b = vhi < g.H ? vhi : g.H;
+        r.tab = 0;
+        if (b <= a) {
+            r.s = r.e = 0;
+            return r;
+        }
+        r.s = off[a - slo];
+        r.e = off[b - slo];
+    }
+    return r;
+}
+
+template <int LAT, int TK, int NT>
+__global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
 {
     extern __shared__ uint4 smem4[];
     __shared__ int s_ok;
-    __shared__ unsigned long long s_red[16];
+    __shared__ unsigned long long s_red[NT / 32];
     const Geom& g = P.g;
     const int64_t RW = g.row_words;
     const int c = blockIdx.x, C = gridDim.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
     const int lo = P.stripe_lo[c], hi = P.stripe_lo[c + 1];
     const bool bot = (c == 0), top = (c == C - 1);
     const int h = P.halo;
     const int slo = bot ? -1 : lo - h;
     const int shi = top ? g.H + 1 : hi + h;
+    const int nloc = shi - slo;
+    constexpr int NTAB = (LAT == LAT_SIXV) ? 2 : 1;
+
+    // shared memory carve-up: rows | random planes | item table | offsets
     uint32_t* sm = reinterpret_cast<uint32_t*>(smem4);
     uint32_t* srow0 = sm - (int64_t)slo * RW;   // srow0 + y * RW is global row y
+    uint4* rbuf = reinterpret_cast<uint4*>(sm + (int64_t)nloc * RW);
+    uint32_t* items = reinterpret_cast<uint32_t*>(rbuf + (size_t)P.npre * P.cap_cycle);
+    int* off = reinterpret_cast<int*>(items + P.cap_items);
 
-    copy_rows_from_global(sm, P.rows0 + (int64_t)slo * RW, (int64_t)(shi - slo) * RW, tid, nt);
+    copy_rows_from_global(sm, P.rows0 + (int64_t)slo * RW, (int64_t)nloc * RW, tid, NT);
+
+    // item tables: active groups of each local row (six-vertex: one table per
+    // face-row parity), prefix offsets per table
+    for (int t = 0; t < NTAB; ++t)
+        for (int r = tid; r < nloc; r += NT) {
+            const int y = slo + r;
+            int cnt = 0;
+            if (y >= 0 && y < g.H && (NTAB == 1 || (y & 1) == t)) {
+                const int2 gr = P.grange[y];
+                cnt = gr.y > gr.x ? gr.y - gr.x : 0;
+            }
+            off[t * (nloc + 1) + r + 1] = cnt;
+        }
+    __syncthreads();
+    if (tid == 0) {
+        // absolute offsets: the tables are stored one after the other
+        int run = 0;
+        for (int t = 0; t < NTAB; ++t) {
+            int* o = off + t * (nloc + 1);
+            o[0] = run;
+            for (int r = 0; r < nloc; ++r) o[r + 1] += o[r];
+            run = o[nloc];
+        }
+    }
+    __syncthreads();
+    for (int t = 0; t < NTAB; ++t)
+        for (int r = tid; r < nloc; r += NT) {
+            const int y = slo + r;
+            if (y < 0 || y >= g.H || (NTAB == 2 && (y & 1) != t)) continue;
+            const int2 gr = P.grange[y];
+            int o = off[t * (nloc + 1) + r];
+            for (int m = gr.x; m < gr.y; ++m) items[o++] = ((uint32_t)r << 8) | (uint32_t)m;
+        }
     __syncthreads();
 
     const int passes = g.passes;
     const uint64_t total = (uint64_t)P.nsweeps * passes;
     const size_t side_words = (size_t)h * RW;
+    const int cap = P.cap_cycle;
     uint64_t done = 0;
     int cyc = 0;
     while (done < total) {
         const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
+
+        // ---- phase 1: random planes of every group of this cycle ----
+        int base = 0;
         for (int i = 1; i <= hc; ++i) {
             const uint64_t pidx = done + (uint64_t)(i - 1);
             const uint32_t sweep = P.sweep0 + (uint32_t)(pidx / passes);
             const uint32_t pass = (uint32_t)(pidx % passes);
-            // rows [vlo, vhi) are exact before this pass
-            const int vlo = bot ? -1 : slo + (i - 1);
-            const int vhi = top ? g.H + 1 : shi - (i - 1);
-            int r0, nrows, rstep;
-            if (LAT == LAT_SIXV) {
-                // face rows Y with vertex rows Y and Y+1 exact, of this class's parity
-                int a = vlo > 1 ? vlo : 1;
-                const int last = (vhi - 2) < (g.N - 1) ? (vhi - 2) : (g.N - 1);
-                if ((a & 1) != sixv_py(pass)) ++a;
-                r0 = a;
-                rstep = 2;
-                nrows = last >= a ? (last - a) / 2 + 1 : 0;
-            } else {
-                const int a = (vlo + 1) > 0 ? (vlo + 1) : 0;
-                const int b = vhi < g.H ? vhi : g.H;
-                r0 = a;
-                rstep = 1;
-                nrows = b > a ? b - a : 0;
-            }
-            const int items = nrows * g.Kg;
-            for (int it = tid; it < items; it += nt) {
-                const int ri = it / g.Kg, m = it - ri * g.Kg;
-                const int y = r0 + ri * rstep;
-                const int2 gr = P.grange[y];
-                if (m < gr.x || m >= gr.y) continue;
+            const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
+            const int n = pr.e - pr.s;
+            for (int it = tid; it < n; it += NT) {
+                const uint32_t item = items[pr.s + it];
+                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                 const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, grp, sweep, P.rng, P.th);
+                for (int k = 0; k < P.npre; ++k)
+                    rbuf[(size_t)k * cap + base + it] =
+                        philox10(grp, sweep, ((uint32_t)k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
             }
+            base += n;
+        }
+        __syncthreads();
+
+        // ---- phase 2: the passes ----
+        base = 0;
+        for (int i = 1; i <= hc; ++i) {
+            const uint64_t pidx = done + (uint64_t)(i - 1);
+            const uint32_t sweep = P.sweep0 + (uint32_t)(pidx / passes);
+            const uint32_t pass = (uint32_t)(pidx % passes);
+            const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
+            const int n = pr.e - pr.s;
+            for (int it = tid; it < n; it += NT) {
+                const uint32_t item = items[pr.s + it];
+                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+                const RndPre rnd{rbuf + base + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
+                group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th);
+            }
+            base += n;
             __syncthreads();
             if (pass == (uint32_t)(passes - 1)) {
                 // end of a sweep: the owned rows are exact (i <= halo)
@@ -137,10 +235,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResParams P)
                                     (ndone - P.burn) % P.stride == 0;
                 if (P.ring || sample) {
                     const int64_t nw = (int64_t)(hi - lo) * RW;
-                    const uint32_t* base = srow0 + (int64_t)lo * RW;
+                    const uint32_t* rb = srow0 + (int64_t)lo * RW;
                     uint64_t acc = 0;
-                    for (int64_t w = tid; w < nw; w += nt) {
-                        const uint32_t v = base[w];
+                    for (int64_t w = tid; w < nw; w += NT) {
+                        const uint32_t v = rb[w];
                         if (!v) continue;
                         const int yy = lo + (int)(w / RW);
                         const int rem = (int)(w - (int64_t)(yy - lo) * RW);
@@ -149,12 +247,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResParams P)
                         if (sample) word_count(v, g, yy, pl, k, P.counts);
                     }
                     if (P.ring) {
-                        for (int off = 16; off; off >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, off);
+                        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
                         if ((tid & 31) == 0) s_red[tid >> 5] = acc;
                         __syncthreads();
                         if (tid == 0) {
                             unsigned long long t = 0;
-                            for (int wv = 0; wv < (nt + 31) / 32; ++wv) t += s_red[wv];
+                            for (int wv = 0; wv < NT / 32; ++wv) t += s_red[wv];
                             atomicAdd(P.ring + (sweep - P.sweep0), t);
                         }
                     }
@@ -165,66 +263,93 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResParams P)
         done += (uint64_t)hc;
         if (done >= total) break;
 
-        // ---- exchange boundary rows with the two neighbouring stripes ----
+        // ---- exchange: tagged 64-bit words, double-buffered by cycle parity ----
         const int par = cyc & 1;
-        uint32_t* mine = P.xbuf + ((size_t)c * 4 + (size_t)par * 2) * side_words;
-        if (!bot) copy_rows_to_global(mine, srow0 + (int64_t)lo * RW, (int64_t)side_words, tid, nt);
-        if (!top) copy_rows_to_global(mine + side_words, srow0 + (int64_t)(hi - h) * RW, (int64_t)side_words, tid, nt);
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned long long want = ((unsigned long long)P.epoch << 32) | (unsigned)(cyc + 1);
-            __threadfence();
-            st_release(P.flags + c, want);
-            int ok = 1;
-            const uint64_t t0 = globaltimer();
-            for (int side = 0; side < 2 && ok; ++side) {
-                if ((side == 0 && bot) || (side == 1 && top)) continue;
-                const unsigned long long* f = P.flags + (side == 0 ? c - 1 : c + 1);
-                while (ld_acquire(f) < want) {
-                    if (*(volatile int*)P.status) { ok = 0; break; }
-                    if (globaltimer() - t0 > kWaitLimitNs) {
+        const unsigned long long tag = ((unsigned long long)((P.epoch & 0xFFFFu) << 16 | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
+        unsigned long long* mine = P.xbuf + ((size_t)c * 4 + (size_t)par * 2) * side_words;
+        if (!bot) {
+            const uint32_t* src = srow0 + (int64_t)lo * RW;
+            for (size_t w = tid; w < side_words; w += NT) st_relaxed(mine + w, tag | src[w]);
+        }
+        if (!top) {
+            const uint32_t* src = srow0 + (int64_t)(hi - h) * RW;
+            for (size_t w = tid; w < side_words; w += NT) st_relaxed(mine + side_words + w, tag | src[w]);
+        }
+        int ok = 1;
+        const uint64_t t0 = globaltimer();
+        for (int side = 0; side < 2; ++side) {
+            if ((side == 0 && bot) || (side == 1 && top)) continue;
+            const unsigned long long* theirs =
+                side == 0 ? P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words
+                          : P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
+            uint32_t* dst = side == 0 ? srow0 + (int64_t)(lo - h) * RW : srow0 + (int64_t)hi * RW;
+            for (size_t w0 = tid; w0 < side_words && ok; w0 += 4 * NT) {
+                // four independent polls in flight per thread
+                unsigned long long v[4];
+                bool have[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const size_t w = w0 + (size_t)u * NT;
+                    have[u] = w >= side_words;
+                    v[u] = have[u] ? tag : ld_relaxed(theirs + w);
+                }
+                for (;;) {
+                    bool all = true;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const size_t w = w0 + (size_t)u * NT;
+                        if (!have[u]) {
+                            if ((v[u] & 0xFFFFFFFF00000000ull) == tag) {
+                                dst[w] = (uint32_t)v[u];
+                                have[u] = true;
+                            } else {
+                                all = false;
+                            }
+                        }
+                    }
+                    if (all) break;
+                    if (*(volatile int*)P.status || globaltimer() - t0 > kWaitLimitNs) {
                         atomicExch(P.status, 1);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(20);
+                    __nanosleep(32);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (!have[u]) v[u] = ld_relaxed(theirs + w0 + (size_t)u * NT);
                 }
             }
-            s_ok = ok;
         }
+        if (tid == 0) s_ok = 1;
+        __syncthreads();
+        if (!ok) s_ok = 0;
         __syncthreads();
         if (!s_ok) return;   // the state is undefined; the host reports TL_ETIMEOUT
-        if (!bot) {
-            const uint32_t* theirs = P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words;
-            copy_rows_from_global(srow0 + (int64_t)(lo - h) * RW, theirs, (int64_t)side_words, tid, nt);
-        }
-        if (!top) {
-            const uint32_t* theirs = P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
-            copy_rows_from_global(srow0 + (int64_t)hi * RW, theirs, (int64_t)side_words, tid, nt);
-        }
-        __syncthreads();
         ++cyc;
     }
-    copy_rows_to_global(P.rows0 + (int64_t)lo * RW, srow0 + (int64_t)lo * RW, (int64_t)(hi - lo) * RW, tid, nt);
+    copy_rows_to_global(P.rows0 + (int64_t)lo * RW, srow0 + (int64_t)lo * RW, (int64_t)(hi - lo) * RW, tid, NT);
 }
 
 template <int LAT, int TK>
-static const void* kernel_ptr()
+static const void* kernel_ptr(int threads)
 {
-    return reinterpret_cast<const void*>(&resident_kernel<LAT, TK>);
+    return threads > 512 ? reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 1024>)
+                         : reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 512>);
 }
 
-static const void* pick(int lattice, int tk)
+static const void* pick(int lattice, int tk, int threads)
 {
-    if (lattice == LAT_DOMINO) return tk == THR_SITE ? kernel_ptr<LAT_DOMINO, THR_SITE>() : kernel_ptr<LAT_DOMINO, THR_SCALAR>();
-    if (lattice == LAT_LOZENGE) return tk == THR_SITE ? kernel_ptr<LAT_LOZENGE, THR_SITE>() : kernel_ptr<LAT_LOZENGE, THR_SCALAR>();
-    return kernel_ptr<LAT_SIXV, THR_TABLE>();
+    if (lattice == LAT_DOMINO)
+        return tk == THR_SITE ? kernel_ptr<LAT_DOMINO, THR_SITE>(threads) : kernel_ptr<LAT_DOMINO, THR_SCALAR>(threads);
+    if (lattice == LAT_LOZENGE)
+        return tk == THR_SITE ? kernel_ptr<LAT_LOZENGE, THR_SITE>(threads) : kernel_ptr<LAT_LOZENGE, THR_SCALAR>(threads);
+    return kernel_ptr<LAT_SIXV, THR_TABLE>(threads);
 }
 
 int resident_prepare(const Geom& g, int thr_kind, int threads, size_t smem_bytes, int* blocks_per_sm)
 {
     *blocks_per_sm = 0;
-    const void* k = pick(g.lattice, thr_kind);
+    const void* k = pick(g.lattice, thr_kind, threads);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -245,13 +370,15 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     P.g = g;
     P.stripe_lo = plan.stripe_lo;
     P.halo = plan.halo;
+    P.npre = plan.npre;
+    P.cap_items = plan.cap_items;
+    P.cap_cycle = plan.cap_cycle;
     P.sweep0 = sweep0;
     P.nsweeps = nsweeps;
     P.rng = rng;
     P.th = th;
     P.grange = grange;
     P.xbuf = plan.xbuf;
-    P.flags = plan.flags;
     P.status = plan.status;
     P.ring = ring;
     P.counts = counts;
@@ -259,7 +386,7 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     P.stride = stride;
     P.epoch = epoch;
     void* args[] = {&P};
-    const void* k = pick(g.lattice, th.kind);
+    const void* k = pick(g.lattice, th.kind, plan.threads);
     return (int)cudaLaunchCooperativeKernel(k, dim3(plan.ctas), dim3(plan.threads), args, plan.smem_bytes,
                                             reinterpret_cast<cudaStream_t>(stream));
 }

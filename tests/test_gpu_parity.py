@@ -47,8 +47,8 @@ def _lat(kind):
     return {"aztec": O.DOMINO, "rect": O.DOMINO, "hex": O.LOZENGE, "dwbc": O.SIXV}[kind]
 
 
-def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, halo=0, scalar=None,
-              site=None, w6=None, hashed=True):
+def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, halo=0, threads=0,
+              npre=0, scalar=None, site=None, w6=None, hashed=True):
     dom = _domain(T, kind, args)
     lat = _lat(kind)
     if lat == O.SIXV:
@@ -62,8 +62,8 @@ def _run_pair(T, ctx, kind, args, *, seed, stream=0, k, kernel=0, spl=0, halo=0,
         th = T.thresholds(scalar=scalar)
         okw = dict(t_scalar=scalar)
     ch = T.Chain(ctx, dom, seed=seed, stream_id=stream, th=th)
-    if kernel or spl or halo:
-        ch.set_plan(kernel, spl, halo)
+    if kernel or spl or halo or threads or npre:
+        ch.set_plan(kernel, spl, halo, threads, npre)
     st = _oracle_state(kind, args)
     if hashed:
         ring = ch.run_hashed(k)
@@ -150,6 +150,14 @@ def test_global_per_pass_kernel(T, ctx, kind, args):
 def test_resident_kernel_halos(T, ctx, kind, args, halo):
     kw = dict(w6=SQ2) if kind == "dwbc" else dict(scalar=(1 << 31) if kind == "aztec" else 0x7FF80000)
     _run_pair(T, ctx, kind, args, seed=23, k=25, kernel=2, halo=halo, **kw)
+
+
+@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("npre", [1, 2, 4])
+@pytest.mark.parametrize("kind,args", [("aztec", (90,)), ("hex", (60, 70, 50)), ("dwbc", (150,))])
+def test_resident_kernel_threads_npre(T, ctx, kind, args, threads, npre):
+    kw = dict(w6=SQ2) if kind == "dwbc" else dict(scalar=(1 << 31) if kind == "aztec" else 0x7FF80000)
+    _run_pair(T, ctx, kind, args, seed=29, k=20, kernel=2, threads=threads, npre=npre, **kw)
 
 
 @pytest.mark.parametrize("spl", [1, 4, 7])
