@@ -188,15 +188,14 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     const int cap = P.cap_cycle;
     uint64_t done = 0;
     int cyc = 0;
+    uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
     while (done < total) {
         const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
 
         // ---- phase 1: random planes of every group of this cycle ----
         int base = 0;
+        uint32_t sweep = cyc_sweep, pass = cyc_pass;
         for (int i = 1; i <= hc; ++i) {
-            const uint64_t pidx = done + (uint64_t)(i - 1);
-            const uint32_t sweep = P.sweep0 + (uint32_t)(pidx / passes);
-            const uint32_t pass = (uint32_t)(pidx % passes);
             const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
             const int n = pr.e - pr.s;
             for (int it = tid; it < n; it += NT) {
@@ -208,15 +207,18 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                         philox10(grp, sweep, ((uint32_t)k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
             }
             base += n;
+            if (++pass == (uint32_t)passes) {
+                pass = 0;
+                ++sweep;
+            }
         }
         __syncthreads();
 
         // ---- phase 2: the passes ----
         base = 0;
+        sweep = cyc_sweep;
+        pass = cyc_pass;
         for (int i = 1; i <= hc; ++i) {
-            const uint64_t pidx = done + (uint64_t)(i - 1);
-            const uint32_t sweep = P.sweep0 + (uint32_t)(pidx / passes);
-            const uint32_t pass = (uint32_t)(pidx % passes);
             const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
             const int n = pr.e - pr.s;
             for (int it = tid; it < n; it += NT) {
@@ -234,17 +236,18 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 const bool sample = P.counts && P.stride && ndone >= P.burn &&
                                     (ndone - P.burn) % P.stride == 0;
                 if (P.ring || sample) {
-                    const int64_t nw = (int64_t)(hi - lo) * RW;
+                    const int rw = (int)RW;
+                    const int nw = (hi - lo) * rw;
                     const uint32_t* rb = srow0 + (int64_t)lo * RW;
                     uint64_t acc = 0;
-                    for (int64_t w = tid; w < nw; w += NT) {
+                    for (int w = tid; w < nw; w += NT) {
                         const uint32_t v = rb[w];
                         if (!v) continue;
-                        const int yy = lo + (int)(w / RW);
-                        const int rem = (int)(w - (int64_t)(yy - lo) * RW);
+                        const int rr = w / rw;
+                        const int rem = w - rr * rw;
                         const int pl = rem / g.K, k = rem - pl * g.K;
-                        if (P.ring) acc += word_hash(v, g, yy, pl, k);
-                        if (sample) word_count(v, g, yy, pl, k, P.counts);
+                        if (P.ring) acc += word_hash(v, g, lo + rr, pl, k);
+                        if (sample) word_count(v, g, lo + rr, pl, k, P.counts);
                     }
                     if (P.ring) {
                         for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
@@ -259,7 +262,13 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     __syncthreads();
                 }
             }
+            if (++pass == (uint32_t)passes) {
+                pass = 0;
+                ++sweep;
+            }
         }
+        cyc_sweep = sweep;
+        cyc_pass = pass;
         done += (uint64_t)hc;
         if (done >= total) break;
 
