@@ -68,6 +68,15 @@ TL_DEV void st_relaxed(unsigned long long* p, unsigned long long v)
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+TL_DEV void ld_relaxed2(const unsigned long long* p, unsigned long long* a, unsigned long long* b)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(*a), "=l"(*b) : "l"(p) : "memory");
+}
+TL_DEV void st_relaxed2(unsigned long long* p, unsigned long long a, unsigned long long b)
+{
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far beyond any healthy exchange
 
 TL_DEV void copy_rows_to_global(uint32_t* dst, const uint32_t* src, int64_t words, int tid, int nt)
@@ -127,6 +136,9 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     extern __shared__ uint4 smem4[];
     __shared__ int s_ok;
     __shared__ unsigned long long s_red[NT / 32];
+    __shared__ int4 s_ptab[64];
+    __shared__ uint32_t s_psweep[64];
+    __shared__ uint32_t s_next_sweep, s_next_pass;
     const Geom& g = P.g;
     const int64_t RW = g.row_words;
     const int c = blockIdx.x, C = gridDim.x;
@@ -186,52 +198,66 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     const uint64_t total = (uint64_t)P.nsweeps * passes;
     const size_t side_words = (size_t)h * RW;
     const int cap = P.cap_cycle;
+    // warp roles: the first half updates the current pass, the second half
+    // generates the random planes of the next pass
+    constexpr int HALF = NT / 2;
+    const bool upd_role = tid < HALF;
+    const int rtid = upd_role ? tid : tid - HALF;
     uint64_t done = 0;
     int cyc = 0;
     uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
     while (done < total) {
         const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
-
-        // ---- phase 1: random planes of every group of this cycle ----
-        int base = 0;
-        uint32_t sweep = cyc_sweep, pass = cyc_pass;
-        for (int i = 1; i <= hc; ++i) {
-            const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
-            const int n = pr.e - pr.s;
-            for (int it = tid; it < n; it += NT) {
-                const uint32_t item = items[pr.s + it];
+        // pass table of this cycle: item range, random-plane slot, sweep, pass
+        if (tid == 0) {
+            uint32_t sweep = cyc_sweep, pass = cyc_pass;
+            int base = 0;
+            for (int i = 1; i <= hc; ++i) {
+                const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
+                s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)pass);
+                s_psweep[i - 1] = sweep;
+                base += pr.e - pr.s;
+                if (++pass == (uint32_t)passes) {
+                    pass = 0;
+                    ++sweep;
+                }
+            }
+            s_next_sweep = sweep;
+            s_next_pass = pass;
+        }
+        __syncthreads();
+        // random planes of one pass (generator warps)
+        auto gen = [&](int i) {
+            const int4 e = s_ptab[i];
+            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
+            for (int it = rtid; it < e.y; it += HALF) {
+                const uint32_t item = items[e.x + it];
                 const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                 const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
                 for (int k = 0; k < P.npre; ++k)
-                    rbuf[(size_t)k * cap + base + it] =
+                    rbuf[(size_t)k * cap + e.z + it] =
                         philox10(grp, sweep, ((uint32_t)k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
             }
-            base += n;
-            if (++pass == (uint32_t)passes) {
-                pass = 0;
-                ++sweep;
-            }
-        }
+        };
+        if (!upd_role) gen(0);
         __syncthreads();
-
-        // ---- phase 2: the passes ----
-        base = 0;
-        sweep = cyc_sweep;
-        pass = cyc_pass;
-        for (int i = 1; i <= hc; ++i) {
-            const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
-            const int n = pr.e - pr.s;
-            for (int it = tid; it < n; it += NT) {
-                const uint32_t item = items[pr.s + it];
-                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
-                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                const RndPre rnd{rbuf + base + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
-                group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th);
+        for (int i = 0; i < hc; ++i) {
+            const int4 e = s_ptab[i];
+            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
+            if (upd_role) {
+                for (int it = rtid; it < e.y; it += HALF) {
+                    const uint32_t item = items[e.x + it];
+                    const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+                    const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+                    const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
+                    group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th);
+                }
+            } else if (i + 1 < hc) {
+                gen(i + 1);
             }
-            base += n;
             __syncthreads();
             if (pass == (uint32_t)(passes - 1)) {
-                // end of a sweep: the owned rows are exact (i <= halo)
+                // end of a sweep: the owned rows are exact (i < halo)
                 const uint64_t ndone = (uint64_t)sweep + 1;
                 const bool sample = P.counts && P.stride && ndone >= P.burn &&
                                     (ndone - P.burn) % P.stride == 0;
@@ -262,70 +288,75 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     __syncthreads();
                 }
             }
-            if (++pass == (uint32_t)passes) {
-                pass = 0;
-                ++sweep;
-            }
         }
-        cyc_sweep = sweep;
-        cyc_pass = pass;
+        cyc_sweep = s_next_sweep;
+        cyc_pass = s_next_pass;
         done += (uint64_t)hc;
         if (done >= total) break;
 
         // ---- exchange: tagged 64-bit words, double-buffered by cycle parity ----
         const int par = cyc & 1;
-        const unsigned long long tag = ((unsigned long long)((P.epoch & 0xFFFFu) << 16 | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
+        const unsigned long long tag =
+            ((unsigned long long)(((P.epoch & 0xFFFFu) << 16) | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
         unsigned long long* mine = P.xbuf + ((size_t)c * 4 + (size_t)par * 2) * side_words;
+        const size_t half = side_words / 2;   // 16-byte units per side (side_words is a multiple of 4)
         if (!bot) {
             const uint32_t* src = srow0 + (int64_t)lo * RW;
-            for (size_t w = tid; w < side_words; w += NT) st_relaxed(mine + w, tag | src[w]);
+            for (size_t w = tid; w < half; w += NT) st_relaxed2(mine + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
         }
         if (!top) {
             const uint32_t* src = srow0 + (int64_t)(hi - h) * RW;
-            for (size_t w = tid; w < side_words; w += NT) st_relaxed(mine + side_words + w, tag | src[w]);
+            for (size_t w = tid; w < half; w += NT)
+                st_relaxed2(mine + side_words + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
         }
+        // every thread polls its 16-byte units of both sides with loads in flight
+        constexpr int MAXU = 4;
         int ok = 1;
-        const uint64_t t0 = globaltimer();
-        for (int side = 0; side < 2; ++side) {
-            if ((side == 0 && bot) || (side == 1 && top)) continue;
-            const unsigned long long* theirs =
-                side == 0 ? P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words
-                          : P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
-            uint32_t* dst = side == 0 ? srow0 + (int64_t)(lo - h) * RW : srow0 + (int64_t)hi * RW;
-            for (size_t w0 = tid; w0 < side_words && ok; w0 += 4 * NT) {
-                // four independent polls in flight per thread
-                unsigned long long v[4];
-                bool have[4];
+        const uint64_t t_wait = globaltimer();
+        const unsigned long long* th0 = bot ? nullptr : P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words;
+        const unsigned long long* th1 = top ? nullptr : P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
+        uint32_t* d0 = srow0 + (int64_t)(lo - h) * RW;
+        uint32_t* d1 = srow0 + (int64_t)hi * RW;
+        const int units = 2 * (int)half;   // both sides
+        for (int u0 = tid; u0 < units && ok; u0 += MAXU * NT) {
+            unsigned long long a[MAXU], b[MAXU];
+            unsigned need = 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const size_t w = w0 + (size_t)u * NT;
-                    have[u] = w >= side_words;
-                    v[u] = have[u] ? tag : ld_relaxed(theirs + w);
+            for (int q = 0; q < MAXU; ++q) {
+                const int u = u0 + q * NT;
+                const bool side = u >= (int)half;
+                const unsigned long long* src = side ? th1 : th0;
+                if (u < units && src != nullptr) {
+                    need |= 1u << q;
+                    ld_relaxed2(src + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
                 }
-                for (;;) {
-                    bool all = true;
+            }
+            while (need) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const size_t w = w0 + (size_t)u * NT;
-                        if (!have[u]) {
-                            if ((v[u] & 0xFFFFFFFF00000000ull) == tag) {
-                                dst[w] = (uint32_t)v[u];
-                                have[u] = true;
-                            } else {
-                                all = false;
-                            }
-                        }
+                for (int q = 0; q < MAXU; ++q) {
+                    if (!(need >> q & 1u)) continue;
+                    if ((a[q] & 0xFFFFFFFF00000000ull) == tag && (b[q] & 0xFFFFFFFF00000000ull) == tag) {
+                        const int u = u0 + q * NT;
+                        const bool side = u >= (int)half;
+                        uint32_t* d = (side ? d1 : d0) + 2 * (u - (side ? (int)half : 0));
+                        d[0] = (uint32_t)a[q];
+                        d[1] = (uint32_t)b[q];
+                        need &= ~(1u << q);
                     }
-                    if (all) break;
-                    if (*(volatile int*)P.status || globaltimer() - t0 > kWaitLimitNs) {
-                        atomicExch(P.status, 1);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
+                }
+                if (!need) break;
+                if (*(volatile int*)P.status || globaltimer() - t_wait > kWaitLimitNs) {
+                    atomicExch(P.status, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (!have[u]) v[u] = ld_relaxed(theirs + w0 + (size_t)u * NT);
+                for (int q = 0; q < MAXU; ++q) {
+                    if (!(need >> q & 1u)) continue;
+                    const int u = u0 + q * NT;
+                    const bool side = u >= (int)half;
+                    ld_relaxed2((side ? th1 : th0) + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
                 }
             }
         }
