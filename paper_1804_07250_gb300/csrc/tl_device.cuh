@@ -217,6 +217,71 @@ TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32
     else store_shl(pHo, Ho, fl, k0);
 }
 
+// Single-plane fast path for dominoes with t = 2^31 (every flippable site
+// goes UP iff the first random plane has a 0 there), used by the resident
+// kernel.  Branch-free over the row parity p and free of atomics: the word of
+// the shifted W plane that straddles two groups (bit 31 of word k0+3 when
+// p = 0) is written entirely by this group, which recomputes the decision of
+// the next group's first site from `onext` (bit 0 of that group's first
+// random word; 0 if that group holds no domain site).  This group therefore
+// never writes bit 31 of word k0-1: the group to its left does, which is why
+// the planner lists one extra group left of every active range.  Because a
+// group reads its neighbours' boundary words, all groups of a pass must
+// finish domino_fast_compute before any of them runs domino_fast_store.
+struct DominoFast {
+    uint32_t* base;      // plane 0 of row y, word k0
+    int64_t soff;        // offset of the S plane row relative to base
+    int K, p;
+    uint4 He, Ho, N, S;  // new values
+};
+
+TL_DEV DominoFast domino_fast_compute(uint32_t* row, int64_t RW, int K, int p, int k0, uint4 o, uint32_t onext)
+{
+    DominoFast r;
+    uint32_t* pHe = row + k0;
+    uint32_t* pHo = row + (size_t)K + k0;
+    uint32_t* pN = row + (size_t)(2 + p) * K + k0;
+    uint32_t* pS = row - RW + (size_t)(2 + p) * K + k0;
+    const uint4 He = ld4(pHe), Ho = ld4(pHo), N = ld4(pN), S = ld4(pS);
+    const uint32_t prev = k0 ? pHo[-1] : 0u;
+    const bool more = k0 + 4 < K;
+    const uint32_t eN = more ? pHe[4] : 0u;                              // Hz_e word k0+4
+    const uint32_t nN = more ? row[(size_t)2 * K + k0 + 4] : 0u;         // Vt_e[y] word k0+4
+    const uint32_t sN = more ? row[-RW + (int64_t)2 * K + k0 + 4] : 0u;  // Vt_e[y-1] word k0+4
+    const uint4 E = p ? Ho : He;
+    const uint4 Wd = p ? He : shl1(Ho, prev);
+    uint4 f;
+    f.x = (E.x & Wd.x & ~(N.x | S.x)) | (N.x & S.x & ~(E.x | Wd.x));
+    f.y = (E.y & Wd.y & ~(N.y | S.y)) | (N.y & S.y & ~(E.y | Wd.y));
+    f.z = (E.z & Wd.z & ~(N.z | S.z)) | (N.z & S.z & ~(E.z | Wd.z));
+    f.w = (E.w & Wd.w & ~(N.w | S.w)) | (N.w & S.w & ~(E.w | Wd.w));
+    // UP iff the plane-0 bit is 0; a flippable site flips iff that differs from E
+    const uint4 fl = make_uint4(f.x & (~o.x ^ E.x), f.y & (~o.y ^ E.y), f.z & (~o.z ^ E.z), f.w & (~o.w ^ E.w));
+    // the next group's first site: its W edge is bit 31 of word k0+3 (p = 0)
+    const uint32_t En = eN & 1u, Wn = Ho.w >> 31, Nn = nN & 1u, Sn = sN & 1u;
+    const uint32_t fn = (En & Wn & ~(Nn | Sn)) | (Nn & Sn & ~(En | Wn));
+    const uint32_t fln = fn & (~onext ^ En) & 1u;
+    const uint4 sh = make_uint4((fl.x >> 1) | (fl.y << 31), (fl.y >> 1) | (fl.z << 31),
+                                (fl.z >> 1) | (fl.w << 31), (fl.w >> 1) | (fln << 31));
+    r.base = pHe;
+    r.soff = -RW + (int64_t)(2 + p) * K;
+    r.K = K;
+    r.p = p;
+    r.He = x4(He, fl);              // E when p = 0, W when p = 1
+    r.Ho = x4(Ho, p ? fl : sh);     // E when p = 1, shifted W when p = 0
+    r.N = x4(N, fl);
+    r.S = x4(S, fl);
+    return r;
+}
+
+TL_DEV void domino_fast_store(const DominoFast& r)
+{
+    st4(r.base, r.He);
+    st4(r.base + r.K, r.Ho);
+    st4(r.base + (size_t)(2 + r.p) * r.K, r.N);
+    st4(r.base + r.soff, r.S);
+}
+
 // ---------------------------------------------------------------------------
 // Lozenges (Sec. 1.2.1).  Row y, class `pass`: sites x = 3j + r with
 // r = (pass - y) mod 3.  Six edges in angular order e0 = E1(x,y),

@@ -124,10 +124,12 @@ struct Canon {
     }
 };
 
+// Groups of a row that hold sites of the domain, plus one group to the left
+// (it owns the word whose top bit is the W edge of the first site).
 static void set_group_range(tl_domain* d, int row, int jmin, int jmax)
 {
     if (jmin > jmax) d->grange[row] = make_int2(0, 0);
-    else d->grange[row] = make_int2(jmin >> 7, (jmax >> 7) + 1);
+    else d->grange[row] = make_int2(std::max(0, (jmin >> 7) - 1), (jmax >> 7) + 1);
 }
 
 // Height rows over a grid of hw x hh points given a membership test for
@@ -586,6 +588,7 @@ struct tl_chain {
     unsigned long long* xbuf_d = nullptr;
     int* status_d = nullptr;
     int threads_req = 0, npre_req = 0;
+    bool no_fast = false;
     unsigned int epoch = 0;
     std::string res_why;
 };
@@ -919,7 +922,7 @@ static int plan_resident(tl_chain* c)
             lo[k] = y;
         }
         lo[C] = g.H;
-        int max_nloc = 0, cap_items = 0, cap_cycle = 0;
+        int max_nloc = 0, cap_items = 0, cap_cycle = 0, max_pass = 0;
         for (int k = 0; k < C; ++k) {
             int slo, shi;
             stripe_local(lo[k], lo[k + 1], k, C, h, g.H, &slo, &shi);
@@ -929,12 +932,15 @@ static int plan_resident(tl_chain* c)
             for (int i = 1; i <= h; ++i) {
                 const int vlo = k == 0 ? -1 : slo + (i - 1);
                 const int vhi = k == C - 1 ? g.H + 1 : shi - (i - 1);
+                int n;
                 if (sixv) {
                     const int a = std::max(vlo, 1), last = std::min(vhi - 2, g.N - 1);
-                    cyc += std::max(items_in(a, last + 1, 0), items_in(a, last + 1, 1));
+                    n = std::max(items_in(a, last + 1, 0), items_in(a, last + 1, 1));
                 } else {
-                    cyc += items_in(vlo + 1, vhi, -1);
+                    n = items_in(vlo + 1, vhi, -1);
                 }
+                cyc += n;
+                max_pass = std::max(max_pass, n);
             }
             cap_cycle = std::max(cap_cycle, cyc);
         }
@@ -945,8 +951,10 @@ static int plan_resident(tl_chain* c)
             c->res_why = "stripe does not fit in shared memory";
             return TL_EUNSUPPORTED;
         }
+        const bool fast = g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
+                          max_pass <= threads && c->npre_req <= 1 && !c->no_fast;
         int bps = 0;
-        if (resident_prepare(g, c->th.kind, threads, smem, &bps) != 0 || bps < 1) {
+        if (resident_prepare(g, c->th.kind, threads, fast, smem, &bps) != 0 || bps < 1) {
             c->res_why = "resident kernel does not fit on an SM";
             return TL_EUNSUPPORTED;
         }
@@ -968,6 +976,7 @@ static int plan_resident(tl_chain* c)
         c->res.npre = npre;
         c->res.cap_items = cap_items;
         c->res.cap_cycle = cap_cycle;
+        c->res.fast = fast;
         c->res.smem_bytes = smem;
         c->res.stripe_lo = c->stripe_d;
         c->res.xbuf = c->xbuf_d;

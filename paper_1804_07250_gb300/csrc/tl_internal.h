@@ -90,6 +90,7 @@ struct ResidentPlan {
     int npre;                      // random planes generated ahead per group
     int cap_items;                 // item-table capacity per CTA
     int cap_cycle;                 // groups touched per cycle, per CTA (upper bound)
+    bool fast;                     // dominoes at t = 2^31: branch-free single-plane update
     size_t smem_bytes;             // dynamic shared memory per CTA
     const int* stripe_lo;          // device [ctas + 1]
     unsigned long long* xbuf;      // device [ctas][2][2][halo][row_words] tagged words
@@ -98,7 +99,7 @@ struct ResidentPlan {
 
 // Shared-memory attribute and occupancy for the resident kernel of this
 // lattice / threshold kind: blocks that fit on one SM (0 if none).
-int resident_prepare(const Geom& g, int thr_kind, int threads, size_t smem_bytes, int* blocks_per_sm);
+int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t smem_bytes, int* blocks_per_sm);
 
 // ring: per-sweep hashes (nullptr = off; must be zeroed).  counts: density
 // counters sampled after every sweep s with s + 1 >= burn and

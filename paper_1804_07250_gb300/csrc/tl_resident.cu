@@ -130,7 +130,9 @@ TL_DEV PassRange pass_range(const Geom& g, int i, uint32_t pass, int slo, int sh
     return r;
 }
 
-template <int LAT, int TK, int NT>
+// FAST: dominoes at t = 2^31 with the branch-free, atomic-free group update;
+// every updater thread handles at most two groups per pass.
+template <int LAT, int TK, int NT, bool FAST>
 __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
 {
     extern __shared__ uint4 smem4[];
@@ -244,7 +246,28 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         for (int i = 0; i < hc; ++i) {
             const int4 e = s_ptab[i];
             const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
-            if (upd_role) {
+            if (FAST && upd_role) {
+                // read and decide every group of the pass, then store: groups
+                // read their neighbours' boundary words
+                DominoFast r0, r1;
+                const bool has0 = rtid < e.y, has1 = rtid + HALF < e.y;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int it = rtid + q * HALF;
+                    if (it >= e.y) break;
+                    const uint32_t item = items[e.x + it];
+                    const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+                    const uint32_t onext =
+                        (it + 1 < e.y && items[e.x + it + 1] == item + 1u) ? rbuf[e.z + it + 1].x : 0u;
+                    const DominoFast r = domino_fast_compute(srow0 + (int64_t)y * RW, RW, g.K,
+                                                             (int)((pass + (uint32_t)y) & 1u), m << 2,
+                                                             rbuf[e.z + it], onext);
+                    if (q == 0) r0 = r; else r1 = r;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(HALF) : "memory");
+                if (has0) domino_fast_store(r0);
+                if (has1) domino_fast_store(r1);
+            } else if (upd_role) {
                 for (int it = rtid; it < e.y; it += HALF) {
                     const uint32_t item = items[e.x + it];
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
@@ -373,12 +396,15 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
 template <int LAT, int TK>
 static const void* kernel_ptr(int threads)
 {
-    return threads > 512 ? reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 1024>)
-                         : reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 512>);
+    return threads > 512 ? reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 1024, false>)
+                         : reinterpret_cast<const void*>(&resident_kernel<LAT, TK, 512, false>);
 }
 
-static const void* pick(int lattice, int tk, int threads)
+static const void* pick(int lattice, int tk, int threads, bool fast = false)
 {
+    if (fast)
+        return threads > 512 ? reinterpret_cast<const void*>(&resident_kernel<LAT_DOMINO, THR_SCALAR, 1024, true>)
+                             : reinterpret_cast<const void*>(&resident_kernel<LAT_DOMINO, THR_SCALAR, 512, true>);
     if (lattice == LAT_DOMINO)
         return tk == THR_SITE ? kernel_ptr<LAT_DOMINO, THR_SITE>(threads) : kernel_ptr<LAT_DOMINO, THR_SCALAR>(threads);
     if (lattice == LAT_LOZENGE)
@@ -386,10 +412,10 @@ static const void* pick(int lattice, int tk, int threads)
     return kernel_ptr<LAT_SIXV, THR_TABLE>(threads);
 }
 
-int resident_prepare(const Geom& g, int thr_kind, int threads, size_t smem_bytes, int* blocks_per_sm)
+int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t smem_bytes, int* blocks_per_sm)
 {
     *blocks_per_sm = 0;
-    const void* k = pick(g.lattice, thr_kind, threads);
+    const void* k = pick(g.lattice, thr_kind, threads, fast);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -426,7 +452,7 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     P.stride = stride;
     P.epoch = epoch;
     void* args[] = {&P};
-    const void* k = pick(g.lattice, th.kind, plan.threads);
+    const void* k = pick(g.lattice, th.kind, plan.threads, plan.fast);
     return (int)cudaLaunchCooperativeKernel(k, dim3(plan.ctas), dim3(plan.threads), args, plan.smem_bytes,
                                             reinterpret_cast<cudaStream_t>(stream));
 }
