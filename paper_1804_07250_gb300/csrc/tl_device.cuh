@@ -235,13 +235,15 @@ struct DominoFast {
     uint4 He, Ho, N, S;  // new values
 };
 
-TL_DEV DominoFast domino_fast_compute(uint32_t* row, int64_t RW, int K, int p, int k0, uint4 o, uint32_t onext)
+// `gp` points at plane 0, word k0 of the group's row.
+TL_DEV DominoFast domino_fast_compute(uint32_t* gp, int64_t RW, int K, int p, int k0, uint4 o, uint32_t onext)
 {
     DominoFast r;
-    uint32_t* pHe = row + k0;
-    uint32_t* pHo = row + (size_t)K + k0;
-    uint32_t* pN = row + (size_t)(2 + p) * K + k0;
-    uint32_t* pS = row - RW + (size_t)(2 + p) * K + k0;
+    uint32_t* row = gp - k0;
+    uint32_t* pHe = gp;
+    uint32_t* pHo = gp + K;
+    uint32_t* pN = gp + (size_t)(2 + p) * K;
+    uint32_t* pS = gp - RW + (size_t)(2 + p) * K;
     const uint4 He = ld4(pHe), Ho = ld4(pHo), N = ld4(pN), S = ld4(pS);
     const uint32_t prev = k0 ? pHo[-1] : 0u;
     const bool more = k0 + 4 < K;

@@ -877,7 +877,7 @@ static int plan_resident(tl_chain* c)
     const Geom& g = c->g;
     const tl_domain& d = c->dom_copy;
     const int h = c->halo_req > 0 ? c->halo_req : default_halo(g);
-    const int threads = c->threads_req > 0 ? c->threads_req : (g.lattice == LAT_DOMINO ? 1024 : 512);
+    const int threads = c->threads_req > 0 ? c->threads_req : 512;
     const int npre = c->npre_req > 0 ? c->npre_req : default_npre(c);
     const bool sixv = g.lattice == LAT_SIXV;
     std::vector<int> act(g.H, 0);
@@ -945,14 +945,15 @@ static int plan_resident(tl_chain* c)
             cap_cycle = std::max(cap_cycle, cyc);
         }
         const int ntab = sixv ? 2 : 1;
-        const size_t smem = (size_t)max_nloc * row_bytes + (size_t)npre * cap_cycle * 16 + (size_t)cap_items * 4 +
-                            (size_t)ntab * (max_nloc + 1) * 4 + 16;
+        const bool fast = g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
+                          max_pass <= threads && c->npre_req <= 1 && !c->no_fast;
+        size_t smem = (size_t)max_nloc * row_bytes + (size_t)npre * cap_cycle * 16 + (size_t)cap_items * 4 +
+                      (size_t)ntab * (max_nloc + 1) * 4 + 16;
+        if (fast) smem += (size_t)cap_items * 8 + 8;
         if ((long)smem > (long)c->ctx->smem_optin) {
             c->res_why = "stripe does not fit in shared memory";
             return TL_EUNSUPPORTED;
         }
-        const bool fast = g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
-                          max_pass <= threads && c->npre_req <= 1 && !c->no_fast;
         int bps = 0;
         if (resident_prepare(g, c->th.kind, threads, fast, smem, &bps) != 0 || bps < 1) {
             c->res_why = "resident kernel does not fit on an SM";

@@ -159,6 +159,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     uint4* rbuf = reinterpret_cast<uint4*>(sm + (int64_t)nloc * RW);
     uint32_t* items = reinterpret_cast<uint32_t*>(rbuf + (size_t)P.npre * P.cap_cycle);
     int* off = reinterpret_cast<int*>(items + P.cap_items);
+    // FAST only: 8-byte aligned after the offsets
+    uint2* fitems = reinterpret_cast<uint2*>((reinterpret_cast<uintptr_t>(off + NTAB * (nloc + 1)) + 7) & ~(uintptr_t)7);
 
     copy_rows_from_global(sm, P.rows0 + (int64_t)slo * RW, (int64_t)nloc * RW, tid, NT);
 
@@ -192,7 +194,14 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             if (y < 0 || y >= g.H || (NTAB == 2 && (y & 1) != t)) continue;
             const int2 gr = P.grange[y];
             int o = off[t * (nloc + 1) + r];
-            for (int m = gr.x; m < gr.y; ++m) items[o++] = ((uint32_t)r << 8) | (uint32_t)m;
+            for (int m = gr.x; m < gr.y; ++m) {
+                if (FAST) {
+                    // word offset of (row y, plane 0, word 4m) and whether m+1 follows in this row
+                    fitems[o] = make_uint2((uint32_t)((int64_t)r * RW + 4 * m),
+                                           (uint32_t)y | ((uint32_t)m << 16) | (m + 1 < gr.y ? 0x80000000u : 0u));
+                }
+                items[o++] = ((uint32_t)r << 8) | (uint32_t)m;
+            }
         }
     __syncthreads();
 
@@ -249,24 +258,25 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             if (FAST && upd_role) {
                 // read and decide every group of the pass, then store: groups
                 // read their neighbours' boundary words
-                DominoFast r0, r1;
-                const bool has0 = rtid < e.y, has1 = rtid + HALF < e.y;
+                constexpr int MAXI = NT >= 1024 ? 1 : 2;
+                DominoFast r[MAXI];
+                bool has[MAXI];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < MAXI; ++q) {
                     const int it = rtid + q * HALF;
-                    if (it >= e.y) break;
-                    const uint32_t item = items[e.x + it];
-                    const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
-                    const uint32_t onext =
-                        (it + 1 < e.y && items[e.x + it + 1] == item + 1u) ? rbuf[e.z + it + 1].x : 0u;
-                    const DominoFast r = domino_fast_compute(srow0 + (int64_t)y * RW, RW, g.K,
-                                                             (int)((pass + (uint32_t)y) & 1u), m << 2,
-                                                             rbuf[e.z + it], onext);
-                    if (q == 0) r0 = r; else r1 = r;
+                    has[q] = it < e.y;
+                    if (!has[q]) continue;
+                    // {smem word offset of (y, k0), y | m << 16 | next-adjacent << 31}
+                    const uint2 fi = fitems[e.x + it];
+                    const int y = (int)(fi.y & 0xFFFFu), m = (int)((fi.y >> 16) & 0xFFu);
+                    const uint32_t onext = (fi.y >> 31) ? rbuf[e.z + it + 1].x : 0u;
+                    r[q] = domino_fast_compute(sm + fi.x, RW, g.K, (int)((pass + (uint32_t)y) & 1u), m << 2,
+                                               rbuf[e.z + it], onext);
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(HALF) : "memory");
-                if (has0) domino_fast_store(r0);
-                if (has1) domino_fast_store(r1);
+#pragma unroll
+                for (int q = 0; q < MAXI; ++q)
+                    if (has[q]) domino_fast_store(r[q]);
             } else if (upd_role) {
                 for (int it = rtid; it < e.y; it += HALF) {
                     const uint32_t item = items[e.x + it];
