@@ -95,6 +95,7 @@ _SIG = {
     "tl_write_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
     "tl_state_hash": (_i, [_vp, _vp, _vp]),
     "tl_read_height": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "tl_read_height_noalloc": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
     "tl_density_begin": (_i, [_vp, _u32, _u64]),
     "tl_read_density": (_i, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "tl_read_domino_nsew": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -325,6 +326,12 @@ class Chain:
             out = np.zeros(self.domain.height_shape, dtype=np.int32)
         p, n = _ptr(out)
         _check(_lib.tl_read_height(self._h, p, n // 4, _stream(stream)))
+        return out
+
+    def read_height_noalloc(self, out, stream=None):
+        """Heights into a device buffer without any allocation (static scratch)."""
+        p, n = _ptr(out)
+        _check(_lib.tl_read_height_noalloc(self._h, p, n // 4, _stream(stream)))
         return out
 
     def density_begin(self, stride: int, burn_in: int = 0):

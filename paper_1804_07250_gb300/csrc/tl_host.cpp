@@ -1194,6 +1194,26 @@ TL_API int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream)
     return TL_OK;
 }
 
+TL_API int tl_read_height_noalloc(tl_chain* c, int32_t* out, size_t cap, void* stream)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_read_height_noalloc: NULL argument");
+    const tl_domain& d = c->dom_copy;
+    const size_t n = (size_t)d.hw * d.hh;
+    if (cap < n) return fail(TL_EINVAL, "tl_read_height_noalloc: cap %zu < %zu", cap, n);
+    if (d.hh > noalloc_height_max_rows())
+        return fail(TL_EINVAL, "tl_read_height_noalloc: %d height rows exceed the static scratch limit of %d",
+                    d.hh, noalloc_height_max_rows());
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (!is_device_ptr(out))
+        return fail(TL_EINVAL, "tl_read_height_noalloc: `out` must be device memory (a host buffer would "
+                               "need a staging allocation)");
+    const int e = launch_height_noalloc(c->g, c->rows, c->hxlo, c->hxhi, c->hspine, d.hw, d.hh, out,
+                                        c->ctx->device, stream);
+    if (e) return fail(TL_ECUDA, "tl_read_height_noalloc: %s", cudaGetErrorString((cudaError_t)e));
+    c->launches += 3;
+    return TL_OK;
+}
+
 TL_API int tl_density_begin(tl_chain* c, uint32_t stride, uint64_t burn_in)
 {
     if (!c || stride == 0) return fail(TL_EINVAL, "tl_density_begin: bad argument");

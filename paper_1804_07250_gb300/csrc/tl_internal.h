@@ -75,6 +75,10 @@ int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int
                   void* stream);
 int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t* planes,
                             void* stream);
+// Height with its row-offset scratch in a static device array (no allocation).
+int noalloc_height_max_rows();
+int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,
+                          int hw, int hh, int32_t* out, int device, void* stream);
 
 // Resident multi-sweep kernel.  One cooperative launch runs `nsweeps`
 // sweeps from absolute sweep `sweep0`.  CTA c owns the rows

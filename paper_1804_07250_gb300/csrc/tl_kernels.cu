@@ -17,6 +17,7 @@
 #include "tl_device.cuh"
 
 #include <cstdint>
+#include <mutex>
 
 namespace tl {
 
@@ -397,6 +398,55 @@ int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int
     height_base_kernel<<<1, 1024, 0, S(stream)>>>(rows0, g, xlo, xhi, spine, hw, hh, out, base_scratch);
     height_add_kernel<<<grid_for((int64_t)hw * hh, 256), 256, 0, S(stream)>>>(out, base_scratch, hw, hh);
     return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Height function without any allocation.  For callers that cannot allocate
+// device memory at the time they need the heights (for example code running
+// under a memory budget that forbids cudaMalloc, or a real-time loop that
+// must not synchronise the device the way cudaMalloc / cudaFree can), the
+// per-row offsets that launch_height keeps in chain-owned memory live here
+// in one file-scope device array instead.  The array holds kNoAllocMaxRows
+// ints (256 KiB), enough for any box this library accepts (at most 65536
+// rows); every GPU that loads the library keeps it until the process exits.
+// All calls on a device share it: each call rewrites every entry it reads,
+// so nothing needs clearing, but calls whose kernels overlap on the GPU
+// (concurrent streams) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxRows = 65536;
+static __device__ __align__(256) int g_noalloc_height_base[kNoAllocMaxRows];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static int* g_noalloc_base_dev[kNoAllocMaxDevices];   // device address per device ordinal
+
+int noalloc_height_max_rows() { return kNoAllocMaxRows; }
+
+// The device address of the scratch array must come from cudaGetSymbolAddress
+// with the device current: in host code the symbol names a host-side stand-in.
+// Done once per device, on the first call made on it.
+static int noalloc_scratch(int device, int** out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base_dev[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_height_base);
+        if (e != cudaSuccess) return (int)e;
+        g_noalloc_base_dev[device] = static_cast<int*>(p);
+    }
+    *out = g_noalloc_base_dev[device];
+    return 0;
+}
+
+int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,
+                          int hw, int hh, int32_t* out, int device, void* stream)
+{
+    if (hh > kNoAllocMaxRows) return (int)cudaErrorInvalidValue;
+    int* base = nullptr;
+    const int e = noalloc_scratch(device, &base);
+    if (e) return e;
+    return launch_height(g, rows, xlo, xhi, spine, hw, hh, out, base, stream);
 }
 
 }  // namespace tl
