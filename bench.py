@@ -37,6 +37,29 @@ BURN = 50_000
 UNIFORM_T = 1 << 31
 WORKLOAD = "aztec_diamond_n2048_uniform_domino"
 METRIC = "flip attempts/s"
+KERNEL_SOURCES = ["paper_1804_07250_gb300/csrc/tl_resident.cu", "paper_1804_07250_gb300/csrc/tl_device.cuh"]
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources still match the ones it was captured from."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(workload)
+    except Exception:
+        return None
+    if not rec or rec.get("kernel_hash") != kernel_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
 ORACLE_SAMPLE_SWEEPS = 4     # per reference-arm step (bounded CPU sample)
 BASELINE_SAMPLE_SWEEPS = 40  # cpu_baseline sample: about 10-30 s of CPU work
 
@@ -172,18 +195,22 @@ def run_ours(args):
     info = dom.info
     stream = torch.cuda.Stream()
     chain = T.Chain(ctx, dom, seed=SEED, stream_id=0, th=T.thresholds(scalar=UNIFORM_T))
-    if args.kernel or args.spl:
-        chain.set_plan(args.kernel, args.spl)
+    if args.kernel or args.spl or args.halo or args.threads:
+        chain.set_plan(args.kernel, args.spl, args.halo, args.threads)
     H, W = info.height, info.width
     height_dev = torch.empty((H, W), dtype=torch.int32, device="cuda")
     nsew_dev = torch.empty((4, H - 1, W - 1), dtype=torch.float64, device="cuda")
     hash_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
-    def step(s):
+    def step(s, ev=None):
         chain.reset(stream=s)
         chain.density_begin(STRIDE, BURN)
+        if ev:
+            ev[0].record(s)
         chain.run(SWEEPS, stream=s)
+        if ev:
+            ev[1].record(s)
         chain.read_height(height_dev, stream=s)
         chain.read_nsew(nsew_dev, stream=s)
         chain.state_hash(out=hash_dev, stream=s)
@@ -191,24 +218,30 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(stream)
     stream.synchronize()
+    chain.sync(stream)
     ref_hash = int(hash_dev.cpu().numpy().view(np.uint64)[0])
 
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = chain.launches
-    total_ms = 0.0
+    total_ms, run_ms, run_launches = 0.0, 0.0, 0
     for _ in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (not timed)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = chain.launches
         e0.record(stream)
-        step(stream)
+        step(stream, (r0, r1))
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         total_ms += e0.elapsed_time(e1)
+        run_ms += r0.elapsed_time(r1)
+        run_launches += 1
     clocks = sampler.stop()
+    chain.sync(stream)
     launches = chain.launches - launches0
     got_hash = int(hash_dev.cpu().numpy().view(np.uint64)[0])
     assert got_hash == ref_hash, "steps are not deterministic"
@@ -219,29 +252,16 @@ def run_ours(args):
     attempts_step = info.sites * SWEEPS
     value = world * attempts_step * args.steps / (total_ms / 1e3)
 
-    # dominant kernel: the sweep kernel, timed alone on the same stream
-    chain.reset(stream=stream)
-    chain.run(1000, stream=stream)
-    stream.synchronize()
-    k_sweeps = 2000
-    l0 = chain.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    chain.run(k_sweeps, stream=stream)
-    e1.record(stream)
-    stream.synchronize()
-    k_launches = chain.launches - l0
-    k_ms = e0.elapsed_time(e1) / k_launches
+    # dominant kernel: the sweep launch of each step (one resident launch of
+    # SWEEPS sweeps), timed with CUDA events on its stream
+    plan = chain.plan()
+    k_launches_per_run = 1 if plan["kernel"] == 2 else SWEEPS * info.passes
+    k_ms = run_ms / run_launches / k_launches_per_run
     bytes_per_sweep = 2 * info.edges / 8
-    alg_bytes_launch = bytes_per_sweep * k_sweeps / k_launches
+    alg_bytes_launch = bytes_per_sweep * SWEEPS / k_launches_per_run
     peak, peak_kind = peaks()
     achieved = alg_bytes_launch / (k_ms / 1e3) / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(WORKLOAD)
-    except Exception:
-        pass
+    traffic = recorded_traffic(WORKLOAD) if plan["kernel"] == 2 else None
 
     # end to end through the C-ABI with host buffers
     init_host = dom.initial_state()
@@ -261,6 +281,7 @@ def run_ours(args):
         chain.read_height(h_out, stream=stream)
         chain.read_nsew(n_out, stream=stream)
     torch.cuda.synchronize()
+    chain.sync(stream)
     e2e_s = time.perf_counter() - t0
     e2e_value = world * attempts_step * e2e_steps / e2e_s
 
@@ -285,8 +306,11 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": traffic, "kernel_ms": k_ms,
-                             "alg_bytes_per_launch": alg_bytes_launch},
+                             "traffic": traffic, "kernel": "resident_kernel" if plan["kernel"] == 2
+                             else "pass_global_kernel", "kernel_ms": k_ms,
+                             "alg_bytes_per_launch": alg_bytes_launch,
+                             "us_per_sweep": 1e3 * run_ms / run_launches / SWEEPS,
+                             "kernel_hash": kernel_hash(), "plan": plan},
                 "clocks": clocks,
                 "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "attempts/s",
@@ -306,6 +330,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-pass, 2 resident")
     ap.add_argument("--spl", type=int, default=0, help="sweeps per launch (0 auto)")
+    ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
+    ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
