@@ -235,16 +235,21 @@ struct DominoFast {
     uint4 He, Ho, N, S;  // new values
 };
 
-// Decide one group from its loaded words: He, Ho, N, S (four words each of
-// Hz_even, Hz_odd, Vt_p of row y and Vt_p of row y-1), `prev` = Hz_odd word
-// k0-1, and the next group's first-site words eN = Hz_even, nN = Vt_even(y),
-// sN = Vt_even(y-1) of word k0+4 (all 0 when there is no next group).
-// `gp` points at plane 0, word k0 of the group's row (stores only).
-TL_DEV DominoFast domino_fast_decide(uint32_t* gp, int64_t RW, int K, int p, uint4 He, uint4 Ho, uint4 N,
-                                     uint4 S, uint32_t prev, uint32_t eN, uint32_t nN, uint32_t sN, uint4 o,
-                                     uint32_t onext)
+// `gp` points at plane 0, word k0 of the group's row.
+TL_DEV DominoFast domino_fast_compute(uint32_t* gp, int64_t RW, int K, int p, int k0, uint4 o, uint32_t onext)
 {
     DominoFast r;
+    uint32_t* row = gp - k0;
+    uint32_t* pHe = gp;
+    uint32_t* pHo = gp + K;
+    uint32_t* pN = gp + (size_t)(2 + p) * K;
+    uint32_t* pS = gp - RW + (size_t)(2 + p) * K;
+    const uint4 He = ld4(pHe), Ho = ld4(pHo), N = ld4(pN), S = ld4(pS);
+    const uint32_t prev = k0 ? pHo[-1] : 0u;
+    const bool more = k0 + 4 < K;
+    const uint32_t eN = more ? pHe[4] : 0u;                              // Hz_e word k0+4
+    const uint32_t nN = more ? row[(size_t)2 * K + k0 + 4] : 0u;         // Vt_e[y] word k0+4
+    const uint32_t sN = more ? row[-RW + (int64_t)2 * K + k0 + 4] : 0u;  // Vt_e[y-1] word k0+4
     const uint4 E = p ? Ho : He;
     const uint4 Wd = p ? He : shl1(Ho, prev);
     uint4 f;
@@ -260,7 +265,7 @@ TL_DEV DominoFast domino_fast_decide(uint32_t* gp, int64_t RW, int K, int p, uin
     const uint32_t fln = fn & (~onext ^ En) & 1u;
     const uint4 sh = make_uint4((fl.x >> 1) | (fl.y << 31), (fl.y >> 1) | (fl.z << 31),
                                 (fl.z >> 1) | (fl.w << 31), (fl.w >> 1) | (fln << 31));
-    r.base = gp;
+    r.base = pHe;
     r.soff = -RW + (int64_t)(2 + p) * K;
     r.K = K;
     r.p = p;

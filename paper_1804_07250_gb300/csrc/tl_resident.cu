@@ -256,64 +256,22 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             const int4 e = s_ptab[i];
             const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
             if (FAST && upd_role) {
-                // Read and decide every group of the pass, then store: groups
-                // need their neighbours' boundary words.  Consecutive items
-                // sit in consecutive lanes, so those words come from the
-                // adjacent lane; loads only at warp and row edges.
+                // read and decide every group of the pass, then store: groups
+                // read their neighbours' boundary words
                 constexpr int MAXI = NT >= 1024 ? 1 : 2;
-                const int lane = tid & 31;
                 DominoFast r[MAXI];
                 bool has[MAXI];
 #pragma unroll
                 for (int q = 0; q < MAXI; ++q) {
                     const int it = rtid + q * HALF;
                     has[q] = it < e.y;
-                    uint2 fi = make_uint2(0u, 0u);
-                    uint4 He = make_uint4(0u, 0u, 0u, 0u), Ho = He, N = He, S = He, o = He;
-                    int y = 0, m = 0, p = 0;
-                    uint32_t* gp = sm;
-                    if (has[q]) {
-                        fi = fitems[e.x + it];   // {smem word offset of (y, k0), y | m << 16 | next-active << 31}
-                        y = (int)(fi.y & 0xFFFFu);
-                        m = (int)((fi.y >> 16) & 0xFFu);
-                        p = (int)((pass + (uint32_t)y) & 1u);
-                        gp = sm + fi.x;
-                        He = ld4(gp);
-                        Ho = ld4(gp + g.K);
-                        N = ld4(gp + (size_t)(2 + p) * g.K);
-                        S = ld4(gp - RW + (size_t)(2 + p) * g.K);
-                        o = rbuf[e.z + it];
-                    }
-                    const uint32_t key = has[q] ? ((uint32_t)y << 9 | (uint32_t)m) : 0xFFFFFFFFu;
-                    const uint32_t key_n = __shfl_down_sync(0xFFFFFFFFu, key, 1);
-                    const uint32_t key_p = __shfl_up_sync(0xFFFFFFFFu, key, 1);
-                    const uint32_t he_n = __shfl_down_sync(0xFFFFFFFFu, He.x, 1);
-                    const uint32_t n_n = __shfl_down_sync(0xFFFFFFFFu, N.x, 1);
-                    const uint32_t s_n = __shfl_down_sync(0xFFFFFFFFu, S.x, 1);
-                    const uint32_t o_n = __shfl_down_sync(0xFFFFFFFFu, o.x, 1);
-                    const uint32_t ho_p = __shfl_up_sync(0xFFFFFFFFu, Ho.w, 1);
                     if (!has[q]) continue;
-                    const int k0 = m << 2;
-                    // previous word of the odd horizontal plane (W of the first site)
-                    uint32_t prev = 0u;
-                    if (k0) prev = (lane > 0 && key_p == key - 1u) ? ho_p : gp[g.K - 1];
-                    // next group's first site (its words belong to group m+1)
-                    uint32_t eN = 0u, nN = 0u, sN = 0u, onext = 0u;
-                    if (fi.y >> 31) {
-                        if (lane < 31 && key_n == key + 1u) {
-                            eN = he_n;
-                            nN = n_n;
-                            sN = s_n;
-                            onext = o_n;
-                        } else {
-                            // p = 0 rows read Vt_even (plane 2); p = 1 rows do not use these
-                            eN = gp[4];
-                            nN = gp[(size_t)2 * g.K + 4];
-                            sN = gp[-RW + (int64_t)2 * g.K + 4];
-                            onext = rbuf[e.z + it + 1].x;
-                        }
-                    }
-                    r[q] = domino_fast_decide(gp, RW, g.K, p, He, Ho, N, S, prev, eN, nN, sN, o, onext);
+                    // {smem word offset of (y, k0), y | m << 16 | next-adjacent << 31}
+                    const uint2 fi = fitems[e.x + it];
+                    const int y = (int)(fi.y & 0xFFFFu), m = (int)((fi.y >> 16) & 0xFFu);
+                    const uint32_t onext = (fi.y >> 31) ? rbuf[e.z + it + 1].x : 0u;
+                    r[q] = domino_fast_compute(sm + fi.x, RW, g.K, (int)((pass + (uint32_t)y) & 1u), m << 2,
+                                               rbuf[e.z + it], onext);
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(HALF) : "memory");
 #pragma unroll
