@@ -320,6 +320,48 @@ int tl_chain_sync(tl_chain* c, void* stream);
  * (all kinds).  For accounting in benchmarks. */
 uint64_t tl_chain_launches(const tl_chain* c);
 
+/* ------------------------------------------------------------------------
+ * Batched chains (many independent samples of possibly different domains
+ * and lattices advanced together; the multi-sample experiments of Sec. 4).
+ * A batch references existing chains (it does not own them) and adds a
+ * second device buffer per chain.  tl_batch_run advances every chain by k
+ * sweeps: each launch runs R sweeps on every tile (a stripe of tile_rows
+ * rows plus a halo of R * passes rows) of every chain, tiles taken largest
+ * first from one work list; blocks of `graph_block` sweeps are replayed as a
+ * CUDA graph when `stream` is not the legacy stream.  Every chain ends in
+ * exactly the state, sweep count and hash it would reach with
+ * tl_run_sweeps alone (random numbers are keyed by site, sweep and the
+ * chain's own stream id).  While in a batch, chains must not sample
+ * densities (TL_EINVAL at creation); they may still be read and run alone
+ * between batch calls.
+ * ---------------------------------------------------------------------- */
+typedef struct tl_batch tl_batch;
+
+typedef struct {
+    int tile_rows;          /* rows per tile (0 = keep) */
+    int sweeps_per_launch;  /* R (0 = keep) */
+    int graph_block;        /* sweeps per CUDA-graph block (0 = keep; default 100) */
+    int grid;               /* out: CTAs per launch */
+    int smem_bytes;         /* out: dynamic shared memory per CTA */
+    int ntiles;             /* out: tiles in the work list */
+} tl_batch_plan;
+
+int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out);
+void tl_batch_destroy(tl_batch* b);
+int tl_batch_run(tl_batch* b, uint64_t k, void* stream);
+/* The comparison point: the same kernel launched once per chain per R
+ * sweeps (no batching, no graph). */
+int tl_batch_run_per_chain(tl_batch* b, uint64_t k, void* stream);
+/* State hash of every chain (uint64 out[n], host or device, n >= chains). */
+int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream);
+int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* plan);
+int tl_batch_get_plan(tl_batch* b, tl_batch_plan* plan);
+/* Time every tile height in {32, 64, 128} x R in {1, 2, 4, 8} on the batch
+ * itself for `trial_sweeps` sweeps each, keep the fastest plan; states and
+ * sweep counters are restored afterwards. */
+int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, tl_batch_plan* out);
+uint64_t tl_batch_launches(const tl_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

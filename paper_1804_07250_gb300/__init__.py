@@ -59,6 +59,15 @@ class Plan(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int), ("sweeps_per_launch", ctypes.c_int),
+                ("graph_block", ctypes.c_int), ("grid", ctypes.c_int), ("smem_bytes", ctypes.c_int),
+                ("ntiles", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Thresholds(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("scalar", ctypes.c_uint32),
                 ("site", ctypes.c_void_p), ("table16", ctypes.c_uint32 * 16)]
@@ -97,6 +106,15 @@ _SIG = {
     "tl_read_height": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
     "tl_read_height_noalloc": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
     "tl_density_begin": (_i, [_vp, _u32, _u64]),
+    "tl_batch_create": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "tl_batch_destroy": (None, [_vp]),
+    "tl_batch_run": (_i, [_vp, _u64, _vp]),
+    "tl_batch_run_per_chain": (_i, [_vp, _u64, _vp]),
+    "tl_batch_hashes": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "tl_batch_set_plan": (_i, [_vp, ctypes.POINTER(BatchPlan)]),
+    "tl_batch_get_plan": (_i, [_vp, ctypes.POINTER(BatchPlan)]),
+    "tl_batch_autotune": (_i, [_vp, _u64, _vp, ctypes.POINTER(BatchPlan)]),
+    "tl_batch_launches": (_u64, [_vp]),
     "tl_read_density": (_i, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "tl_read_domino_nsew": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
 }
@@ -363,3 +381,58 @@ class Chain:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many chains advanced together (one work list, CUDA-graph blocks)."""
+
+    def __init__(self, ctx: Context, chains):
+        self.ctx, self.chains = ctx, list(chains)
+        arr = (_vp * len(self.chains))(*[c._h for c in self.chains])
+        self._arr = arr
+        h = _vp()
+        _check(_lib.tl_batch_create(ctx._h, ctypes.cast(arr, _vp), len(self.chains), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, k: int, stream=None):
+        _check(_lib.tl_batch_run(self._h, k, _stream(stream)))
+
+    def run_per_chain(self, k: int, stream=None):
+        _check(_lib.tl_batch_run_per_chain(self._h, k, _stream(stream)))
+
+    def hashes(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(len(self.chains), dtype=np.uint64)
+        p, n = _ptr(out)
+        _check(_lib.tl_batch_hashes(self._h, p, n // 8, _stream(stream)))
+        return out
+
+    def set_plan(self, tile_rows=0, sweeps_per_launch=0, graph_block=0):
+        p = BatchPlan(tile_rows, sweeps_per_launch, graph_block, 0, 0, 0)
+        _check(_lib.tl_batch_set_plan(self._h, ctypes.byref(p)))
+
+    def plan(self) -> dict:
+        p = BatchPlan()
+        _check(_lib.tl_batch_get_plan(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def autotune(self, trial_sweeps: int = 8, stream=None) -> dict:
+        p = BatchPlan()
+        _check(_lib.tl_batch_autotune(self._h, trial_sweeps, _stream(stream), ctypes.byref(p)))
+        return p.as_dict()
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.tl_batch_launches(self._h))
+
+    def close(self):
+        if self._h:
+            _lib.tl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,208 @@
+// Batched chains: one launch advances every tile of every chain by R sweeps.
+//
+// Many independent chains of uneven size (the batched workload of Sec. 4's
+// sampling experiments) are cut into row stripes ("tiles").  A CTA takes
+// tiles from a work list ordered largest first, loads a tile plus a halo of
+// passes * R rows from the chain's source buffer into shared memory, runs the
+// R sweeps there with the exact region shrinking one row per pass, and writes
+// only the tile's own rows to the destination buffer.  Because tiles of one
+// chain run concurrently within a launch, a launch reads one buffer and
+// writes the other; consecutive launches alternate.  Sweep indices come from
+// a per-chain device counter, so a block of launches captured in a CUDA graph
+// can be replayed: the graph ends with a kernel that advances the counters.
+#include "tl_device.cuh"
+
+#include <cstdint>
+
+namespace tl {
+
+template <int LAT, int TK>
+TL_DEV void tile_passes(const BatchChain& ch, uint32_t* srow0, int slo, int shi, bool bot, bool top, uint32_t sweep0,
+                        int R)
+{
+    const Geom& g = ch.g;
+    const int64_t RW = g.row_words;
+    const int passes = g.passes;
+    int i = 0;
+    for (int r = 0; r < R; ++r) {
+        const uint32_t sweep = sweep0 + (uint32_t)r;
+        for (int p = 0; p < passes; ++p, ++i) {
+            const int vlo = bot ? -1 : slo + i;
+            const int vhi = top ? g.H + 1 : shi - i;
+            int a, nrows, step;
+            if (LAT == LAT_SIXV) {
+                a = vlo > 1 ? vlo : 1;
+                const int last = (vhi - 2) < (g.N - 1) ? (vhi - 2) : (g.N - 1);
+                if ((a & 1) != sixv_py((uint32_t)p)) ++a;
+                step = 2;
+                nrows = last >= a ? (last - a) / 2 + 1 : 0;
+            } else {
+                a = (vlo + 1) > 0 ? (vlo + 1) : 0;
+                const int b = vhi < g.H ? vhi : g.H;
+                step = 1;
+                nrows = b > a ? b - a : 0;
+            }
+            const int items = nrows * g.Kg;
+            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+                const int ri = it / g.Kg, m = it - ri * g.Kg;
+                const int y = a + ri * step;
+                const int2 gr = ch.grange[y];
+                if (m < gr.x || m >= gr.y) continue;
+                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+                const RndPhilox rnd{grp, sweep, (uint32_t)p, ch.rng};
+                group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, (uint32_t)p, rnd, ch.th);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_kernel(const BatchChain* __restrict__ chains,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, int R,
+                                                    uint32_t sweep_off, int src, unsigned int* cursor)
+{
+    extern __shared__ uint4 smem4[];
+    __shared__ int s_tile;
+    uint32_t* sm = reinterpret_cast<uint32_t*>(smem4);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(cursor, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const BatchTile tile = tiles[t];
+        const BatchChain& ch = chains[tile.chain];
+        const Geom& g = ch.g;
+        const int64_t RW = g.row_words;
+        const int halo = g.passes * R;
+        const bool bot = tile.lo == 0, top = tile.hi == g.H;
+        const int slo = bot ? -1 : (tile.lo - halo > -1 ? tile.lo - halo : -1);
+        const int shi = top ? g.H + 1 : (tile.hi + halo < g.H + 1 ? tile.hi + halo : g.H + 1);
+        // a halo clamped at a pad row is exact from then on
+        const bool bot_x = slo == -1, top_x = shi == g.H + 1;
+        const uint32_t* srcp = ch.rows[src] + RW;   // global row 0
+        uint32_t* dstp = ch.rows[src ^ 1] + RW;
+        {
+            const uint4* s4 = reinterpret_cast<const uint4*>(srcp + (int64_t)slo * RW);
+            uint4* d4 = reinterpret_cast<uint4*>(sm);
+            const int64_t n4 = (int64_t)(shi - slo) * RW / 4;
+            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldcg(s4 + i);
+        }
+        __syncthreads();
+        const uint32_t sweep0 = *ch.sweep_base + sweep_off;
+        uint32_t* srow0 = sm - (int64_t)slo * RW;
+        if (g.lattice == LAT_DOMINO) {
+            if (ch.th.kind == THR_SITE) tile_passes<LAT_DOMINO, THR_SITE>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
+            else tile_passes<LAT_DOMINO, THR_SCALAR>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
+        } else if (g.lattice == LAT_LOZENGE) {
+            if (ch.th.kind == THR_SITE) tile_passes<LAT_LOZENGE, THR_SITE>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
+            else tile_passes<LAT_LOZENGE, THR_SCALAR>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
+        } else {
+            tile_passes<LAT_SIXV, THR_TABLE>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
+        }
+        {
+            const uint4* s4 = reinterpret_cast<const uint4*>(srow0 + (int64_t)tile.lo * RW);
+            uint4* d4 = reinterpret_cast<uint4*>(dstp + (int64_t)tile.lo * RW);
+            const int64_t n4 = (int64_t)(tile.hi - tile.lo) * RW / 4;
+            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) __stcg(d4 + i, s4[i]);
+        }
+        // the pad rows of the destination stay zero: they are never written
+        __syncthreads();
+    }
+}
+
+__global__ void batch_advance_kernel(const BatchChain* __restrict__ chains, int nchains, uint32_t k,
+                                     unsigned int* cursors, int ncursors)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchains; i += gridDim.x * blockDim.x)
+        *chains[i].sweep_base += k;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncursors; i += gridDim.x * blockDim.x) cursors[i] = 0u;
+}
+
+int batch_prepare(size_t smem_bytes, int* blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return (int)e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem_bytes);
+    if (e != cudaSuccess) cudaGetLastError();
+    return (int)e;
+}
+
+int launch_batch(const BatchChain* chains, const BatchTile* tiles, int ntiles, int R, uint32_t sweep_off, int src,
+                 unsigned int* cursor, int grid, size_t smem_bytes, void* stream)
+{
+    batch_kernel<<<grid, 256, smem_bytes, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles, R,
+                                                                                   sweep_off, src, cursor);
+    return (int)cudaGetLastError();
+}
+
+int launch_batch_advance(const BatchChain* chains, int nchains, uint32_t k, unsigned int* cursors, int ncursors,
+                         void* stream)
+{
+    const int n = nchains > ncursors ? nchains : ncursors;
+    batch_advance_kernel<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(chains, nchains, k,
+                                                                                             cursors, ncursors);
+    return (int)cudaGetLastError();
+}
+
+// Per-chain state hash over all tiles (out[chain] must be zeroed).
+__global__ void batch_hash_kernel(const BatchChain* __restrict__ chains, const BatchTile* __restrict__ tiles,
+                                  int ntiles, int buf, unsigned long long* out)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tile = tiles[t];
+        const BatchChain& ch = chains[tile.chain];
+        const Geom& g = ch.g;
+        const int64_t RW = g.row_words;
+        const uint32_t* base = ch.rows[buf] + RW + (int64_t)tile.lo * RW;
+        const int nw = (tile.hi - tile.lo) * (int)RW;
+        uint64_t acc = 0;
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            const uint32_t v = base[w];
+            if (!v) continue;
+            const int rr = w / (int)RW;
+            const int rem = w - rr * (int)RW;
+            const int pl = rem / g.K, k = rem - pl * g.K;
+            acc += word_hash(v, g, tile.lo + rr, pl, k);
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out + tile.chain, (unsigned long long)acc);
+    }
+}
+
+int launch_batch_hash(const BatchChain* chains, const BatchTile* tiles, int ntiles, int buf,
+                      unsigned long long* out, void* stream)
+{
+    const int grid = ntiles < 4096 ? ntiles : 4096;
+    batch_hash_kernel<<<grid > 0 ? grid : 1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles,
+                                                                                             buf, out);
+    return (int)cudaGetLastError();
+}
+
+// Copy every tile's rows from buffer `from` to the other buffer.
+__global__ void batch_copy_kernel(const BatchChain* __restrict__ chains, const BatchTile* __restrict__ tiles,
+                                  int ntiles, int from)
+{
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tile = tiles[t];
+        const BatchChain& ch = chains[tile.chain];
+        const int64_t RW = ch.g.row_words;
+        const uint4* s4 = reinterpret_cast<const uint4*>(ch.rows[from] + RW + (int64_t)tile.lo * RW);
+        uint4* d4 = reinterpret_cast<uint4*>(ch.rows[from ^ 1] + RW + (int64_t)tile.lo * RW);
+        const int64_t n4 = (int64_t)(tile.hi - tile.lo) * RW / 4;
+        for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+    }
+}
+
+int launch_batch_copy(const BatchChain* chains, const BatchTile* tiles, int ntiles, int from, void* stream)
+{
+    const int grid = ntiles < 4096 ? ntiles : 4096;
+    batch_copy_kernel<<<grid > 0 ? grid : 1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles,
+                                                                                             from);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tl

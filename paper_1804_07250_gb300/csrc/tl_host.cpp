@@ -1275,3 +1275,393 @@ TL_API int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* strea
         return launch_nsew(c->g, c->counts, c->samples, c->kappa, o, stream);
     });
 }
+
+// ---------------------------------------------------------------------------
+// Batched chains
+// ---------------------------------------------------------------------------
+struct tl_batch {
+    tl_ctx* ctx = nullptr;
+    std::vector<tl_chain*> chains;
+    std::vector<BatchChain> hchains;
+    BatchChain* d_chains = nullptr;
+    std::vector<uint32_t*> alt;           // second state buffer of every chain
+    uint32_t* d_sweep = nullptr;          // per-chain sweep counters on the device
+    std::vector<uint32_t> h_sweep;
+    std::vector<BatchTile> tiles_lpt;     // largest first (batched launches)
+    std::vector<BatchTile> tiles_chain;   // grouped by chain (per-chain launches)
+    std::vector<int> chain_first;         // first tile of each chain in tiles_chain
+    BatchTile* d_tiles_lpt = nullptr;
+    BatchTile* d_tiles_chain = nullptr;
+    unsigned int* d_cursor = nullptr;     // one cursor per launch slot
+    int ncursor = 0;
+    unsigned long long* d_hash = nullptr;
+    int tile_rows = 64, R = 2, block = 100, grid = 0;
+    size_t smem = 0;
+    int ntiles = 0;
+    int src = 0;                          // buffer holding the current state
+    uint64_t launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_block = 0;
+};
+
+static void batch_free_plan(tl_batch* b)
+{
+    cudaFree(b->d_tiles_lpt);
+    cudaFree(b->d_tiles_chain);
+    b->d_tiles_lpt = b->d_tiles_chain = nullptr;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+static void batch_free(tl_batch* b)
+{
+    if (!b) return;
+    batch_free_plan(b);
+    for (auto* p : b->alt) cudaFree(p);
+    cudaFree(b->d_chains);
+    cudaFree(b->d_sweep);
+    cudaFree(b->d_cursor);
+    cudaFree(b->d_hash);
+    delete b;
+}
+
+// Tiles of height tile_rows for every chain; shared memory for tile + halo.
+static int batch_plan(tl_batch* b, int tile_rows, int R)
+{
+    if (tile_rows < 1 || R < 1 || R > 64) return fail(TL_EINVAL, "batch plan: tile_rows %d, R %d", tile_rows, R);
+    std::vector<BatchTile> tiles;
+    std::vector<double> work;
+    std::vector<int> first;
+    size_t smem = 0;
+    for (size_t i = 0; i < b->chains.size(); ++i) {
+        const tl_chain* c = b->chains[i];
+        const Geom& g = c->g;
+        const int halo = g.passes * R;
+        first.push_back((int)tiles.size());
+        for (int lo = 0; lo < g.H; lo += tile_rows) {
+            const int hi = std::min(g.H, lo + tile_rows);
+            tiles.push_back(BatchTile{(int)i, lo, hi});
+            const int slo = std::max(lo - halo, -1), shi = std::min(hi + halo, g.H + 1);
+            smem = std::max(smem, (size_t)(shi - slo) * (size_t)g.row_words * 4);
+            double wk = 0;
+            for (int y = std::max(slo, 0); y < std::min(shi, g.H); ++y) {
+                const int2 r = c->dom_copy.grange[y];
+                wk += 0.1 + std::max(0, r.y - r.x);
+            }
+            work.push_back(wk * R);
+        }
+    }
+    first.push_back((int)tiles.size());
+    if ((long)smem > (long)b->ctx->smem_optin) return fail(TL_EUNSUPPORTED, "batch plan: a tile needs %zu B of shared memory", smem);
+    int bps = 0;
+    if (batch_prepare(smem, &bps) != 0 || bps < 1) return fail(TL_EUNSUPPORTED, "batch plan: tile kernel does not fit");
+    std::vector<int> order(tiles.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<BatchTile> lpt(tiles.size());
+    for (size_t i = 0; i < order.size(); ++i) lpt[i] = tiles[order[i]];
+    batch_free_plan(b);
+    TL_TRY(dev_alloc(&b->d_tiles_lpt, lpt.size(), "tiles"));
+    TL_TRY(dev_alloc(&b->d_tiles_chain, tiles.size(), "tiles"));
+    CUDA_TRY(cudaMemcpy(b->d_tiles_lpt, lpt.data(), sizeof(BatchTile) * lpt.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b->d_tiles_chain, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
+    b->tiles_lpt = lpt;
+    b->tiles_chain = tiles;
+    b->chain_first = first;
+    b->ntiles = (int)tiles.size();
+    b->tile_rows = tile_rows;
+    b->R = R;
+    b->smem = smem;
+    b->grid = std::min(bps * b->ctx->sms, b->ntiles);
+    return TL_OK;
+}
+
+TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out)
+{
+    if (!ctx || !chains || !out || n == 0) return fail(TL_EINVAL, "tl_batch_create: bad argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    tl_batch* b = new (std::nothrow) tl_batch();
+    if (!b) return fail(TL_ENOMEM, "tl_batch_create: host allocation");
+    b->ctx = ctx;
+    int rc = TL_OK;
+    for (size_t i = 0; i < n && rc == TL_OK; ++i) {
+        tl_chain* c = chains[i];
+        if (!c || c->ctx->device != ctx->device) rc = fail(TL_EINVAL, "tl_batch_create: chain %zu invalid", i);
+        else if (c->density_on) rc = fail(TL_EINVAL, "tl_batch_create: chain %zu samples densities", i);
+        b->chains.push_back(c);
+    }
+    const int nc = (int)n;
+    b->ncursor = 1024;
+    if (rc == TL_OK && ((rc = dev_alloc(&b->d_chains, n, "batch chains")) || (rc = dev_alloc(&b->d_sweep, n, "sweeps")) ||
+                        (rc = dev_alloc(&b->d_cursor, (size_t)b->ncursor, "cursors")) ||
+                        (rc = dev_alloc(&b->d_hash, n, "hashes")))) {
+    }
+    for (int i = 0; i < nc && rc == TL_OK; ++i) {
+        tl_chain* c = b->chains[i];
+        uint32_t* a = nullptr;
+        rc = dev_alloc(&a, (size_t)c->g.total_words, "second state buffer");
+        if (rc == TL_OK) {
+            b->alt.push_back(a);
+            if (cudaMemset(a, 0, (size_t)c->g.total_words * 4) != cudaSuccess)
+                rc = fail(TL_ECUDA, "tl_batch_create: memset");
+        }
+        BatchChain bc{};
+        bc.g = c->g;
+        bc.rows[0] = c->rows;
+        bc.rows[1] = a;
+        bc.grange = c->grange;
+        bc.th = c->th;
+        bc.rng = c->rng;
+        bc.sweep_base = b->d_sweep + i;
+        b->hchains.push_back(bc);
+        b->h_sweep.push_back((uint32_t)c->sweep);
+    }
+    if (rc == TL_OK && cudaMemcpy(b->d_chains, b->hchains.data(), sizeof(BatchChain) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(TL_ECUDA, "tl_batch_create: upload");
+    if (rc == TL_OK && cudaMemset(b->d_cursor, 0, sizeof(unsigned int) * b->ncursor) != cudaSuccess)
+        rc = fail(TL_ECUDA, "tl_batch_create: memset");
+    if (rc == TL_OK) rc = batch_plan(b, 64, 2);
+    if (rc != TL_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return TL_OK;
+}
+
+TL_API void tl_batch_destroy(tl_batch* b)
+{
+    if (b) cudaSetDevice(b->ctx->device);
+    batch_free(b);
+}
+
+TL_API uint64_t tl_batch_launches(const tl_batch* b) { return b ? b->launches : 0; }
+
+static int batch_upload_sweeps(tl_batch* b, void* stream)
+{
+    for (size_t i = 0; i < b->chains.size(); ++i) {
+        if (b->chains[i]->sweep + 1 > 0xFFFFFFFFull) return fail(TL_EINVAL, "batch: sweep index beyond 2^32");
+        b->h_sweep[i] = (uint32_t)b->chains[i]->sweep;
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_sweep, b->h_sweep.data(), 4 * b->h_sweep.size(), cudaMemcpyHostToDevice, SS(stream)));
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));   // the host vector is pageable
+    return TL_OK;
+}
+
+// One batched launch of r sweeps starting `off` sweeps after the counters.
+static int batch_launch(tl_batch* b, int r, uint32_t off, int slot, void* stream, bool per_chain)
+{
+    unsigned int* cur = b->d_cursor + (slot % b->ncursor);
+    if (!per_chain) {
+        CUDA_TRY(cudaMemsetAsync(cur, 0, 4, SS(stream)));
+        const int e = launch_batch(b->d_chains, b->d_tiles_lpt, b->ntiles, r, off, b->src, cur, b->grid, b->smem, stream);
+        if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
+        b->launches += 1;
+    } else {
+        for (size_t i = 0; i < b->chains.size(); ++i) {
+            const int t0 = b->chain_first[i], nt = b->chain_first[i + 1] - t0;
+            unsigned int* ci = b->d_cursor + ((slot * (int)b->chains.size() + (int)i) % b->ncursor);
+            CUDA_TRY(cudaMemsetAsync(ci, 0, 4, SS(stream)));
+            const int e = launch_batch(b->d_chains, b->d_tiles_chain + t0, nt, r, off, b->src, ci,
+                                       std::min(nt, b->grid), b->smem, stream);
+            if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
+            b->launches += 1;
+        }
+    }
+    b->src ^= 1;
+    return TL_OK;
+}
+
+static int batch_finish(tl_batch* b, uint64_t k, void* stream)
+{
+    // state back in each chain's own buffer; counters advanced
+    if (b->src) {
+        const int e = launch_batch_copy(b->d_chains, b->d_tiles_chain, b->ntiles, 1, stream);
+        if (e) return fail(TL_ECUDA, "batch copy: %s", cudaGetErrorString((cudaError_t)e));
+        b->launches += 1;
+        b->src = 0;
+    }
+    for (auto* c : b->chains) c->sweep += k;
+    return TL_OK;
+}
+
+// Graph of one block of `block` sweeps: the launches plus the counter advance.
+static int batch_build_graph(tl_batch* b, void* stream)
+{
+    if (b->graph && b->graph_block == b->block) return TL_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaStream_t s = SS(stream);
+    if (!s) return TL_OK;   // the legacy stream cannot be captured: run without a graph
+    const int nl = b->block / b->R;
+    const int src0 = b->src;
+    const uint64_t l0 = b->launches;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = TL_OK;
+    for (int j = 0; j < nl && rc == TL_OK; ++j) rc = batch_launch(b, b->R, (uint32_t)(j * b->R), j, stream, false);
+    if (rc == TL_OK) {
+        const int e = launch_batch_advance(b->d_chains, (int)b->chains.size(), (uint32_t)b->block, b->d_cursor, 0, stream);
+        if (e) rc = fail(TL_ECUDA, "batch advance: %s", cudaGetErrorString((cudaError_t)e));
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    b->src = src0;
+    b->launches = l0;
+    if (rc != TL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(TL_ECUDA, "batch graph capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(TL_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(ie));
+    b->graph_block = b->block;
+    return TL_OK;
+}
+
+static int batch_run(tl_batch* b, uint64_t k, void* stream, bool per_chain)
+{
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    if (k == 0) return TL_OK;
+    TL_TRY(batch_upload_sweeps(b, stream));
+    uint64_t done = 0;
+    int slot = 0;
+    // whole graph blocks (an even number of launches, so the state ends where it began)
+    const bool use_graph = !per_chain && b->block % b->R == 0 && (b->block / b->R) % 2 == 0;
+    if (use_graph && k >= (uint64_t)b->block) TL_TRY(batch_build_graph(b, stream));
+    while (use_graph && b->graph && k - done >= (uint64_t)b->block) {
+        CUDA_TRY(cudaGraphLaunch(b->graph, SS(stream)));
+        b->launches += (uint64_t)(b->block / b->R) + 1;
+        done += (uint64_t)b->block;
+    }
+    // the rest: sweeps `done` onwards relative to the counters at the last advance
+    const uint64_t rest_start = done;
+    while (done < k) {
+        const int r = (int)std::min<uint64_t>((uint64_t)b->R, k - done);
+        TL_TRY(batch_launch(b, r, (uint32_t)(done - rest_start), slot++, stream, per_chain));
+        done += (uint64_t)r;
+    }
+    if (k > rest_start) {
+        const int e = launch_batch_advance(b->d_chains, (int)b->chains.size(), (uint32_t)(k - rest_start), b->d_cursor,
+                                           0, stream);
+        if (e) return fail(TL_ECUDA, "batch advance: %s", cudaGetErrorString((cudaError_t)e));
+        b->launches += 1;
+    }
+    return batch_finish(b, k, stream);
+}
+
+TL_API int tl_batch_run(tl_batch* b, uint64_t k, void* stream)
+{
+    if (!b) return fail(TL_EINVAL, "tl_batch_run: NULL batch");
+    return batch_run(b, k, stream, false);
+}
+
+TL_API int tl_batch_run_per_chain(tl_batch* b, uint64_t k, void* stream)
+{
+    if (!b) return fail(TL_EINVAL, "tl_batch_run_per_chain: NULL batch");
+    return batch_run(b, k, stream, true);
+}
+
+TL_API int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream)
+{
+    if (!b || !out || n < b->chains.size()) return fail(TL_EINVAL, "tl_batch_hashes: bad argument");
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    CUDA_TRY(cudaMemsetAsync(b->d_hash, 0, 8 * b->chains.size(), SS(stream)));
+    const int e = launch_batch_hash(b->d_chains, b->d_tiles_chain, b->ntiles, b->src, b->d_hash, stream);
+    if (e) return fail(TL_ECUDA, "batch hash: %s", cudaGetErrorString((cudaError_t)e));
+    b->launches += 1;
+    const bool dev = is_device_ptr(out);
+    CUDA_TRY(cudaMemcpyAsync(out, b->d_hash, 8 * b->chains.size(), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             SS(stream)));
+    if (!dev) CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    return TL_OK;
+}
+
+TL_API int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* p)
+{
+    if (!b || !p) return fail(TL_EINVAL, "tl_batch_set_plan: NULL argument");
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    const int tr = p->tile_rows > 0 ? p->tile_rows : b->tile_rows;
+    const int R = p->sweeps_per_launch > 0 ? p->sweeps_per_launch : b->R;
+    if (p->graph_block > 0) b->block = p->graph_block;
+    CUDA_TRY(cudaDeviceSynchronize());
+    return batch_plan(b, tr, R);
+}
+
+TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
+{
+    if (!b || !p) return fail(TL_EINVAL, "tl_batch_get_plan: NULL argument");
+    p->tile_rows = b->tile_rows;
+    p->sweeps_per_launch = b->R;
+    p->graph_block = b->block;
+    p->grid = b->grid;
+    p->smem_bytes = (int)b->smem;
+    p->ntiles = b->ntiles;
+    return TL_OK;
+}
+
+// Try tile heights x sweeps per launch on the batch itself, keep the fastest.
+// The chains' states and sweep counters are restored afterwards, so tuning
+// does not change any result.
+TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, tl_batch_plan* out)
+{
+    if (!b || trial_sweeps == 0) return fail(TL_EINVAL, "tl_batch_autotune: bad argument");
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    // snapshot every chain's state
+    size_t total = 0;
+    for (auto* c : b->chains) total += (size_t)c->g.total_words;
+    uint32_t* snap = nullptr;
+    TL_TRY(dev_alloc(&snap, total, "autotune snapshot"));
+    size_t o = 0;
+    for (auto* c : b->chains) {
+        CUDA_TRY(cudaMemcpyAsync(snap + o, c->rows, (size_t)c->g.total_words * 4, cudaMemcpyDeviceToDevice, SS(stream)));
+        o += (size_t)c->g.total_words;
+    }
+    std::vector<uint64_t> sweeps;
+    for (auto* c : b->chains) sweeps.push_back(c->sweep);
+    const int tile_opts[] = {32, 64, 128};
+    const int r_opts[] = {1, 2, 4, 8};
+    float best = 1e30f;
+    int best_t = b->tile_rows, best_r = b->R;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = TL_OK;
+    for (int tr : tile_opts)
+        for (int R : r_opts) {
+            if (rc != TL_OK) break;
+            if (batch_plan(b, tr, R) != TL_OK) continue;   // does not fit: skip
+            const uint64_t k = ((trial_sweeps + R - 1) / R) * R;
+            const int saved_block = b->block;
+            b->block = 1 << 30;                            // no graph during trials
+            cudaEventRecord(e0, SS(stream));
+            rc = batch_run(b, k, stream, false);
+            cudaEventRecord(e1, SS(stream));
+            b->block = saved_block;
+            if (rc != TL_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / k < best) {
+                best = ms / k;
+                best_t = tr;
+                best_r = R;
+            }
+            // restore
+            o = 0;
+            for (size_t i = 0; i < b->chains.size(); ++i) {
+                tl_chain* c = b->chains[i];
+                cudaMemcpyAsync(c->rows, snap + o, (size_t)c->g.total_words * 4, cudaMemcpyDeviceToDevice, SS(stream));
+                o += (size_t)c->g.total_words;
+                c->sweep = sweeps[i];
+            }
+        }
+    cudaStreamSynchronize(SS(stream));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (rc != TL_OK) return rc;
+    TL_TRY(batch_plan(b, best_t, best_r));
+    if (out) TL_TRY(tl_batch_get_plan(b, out));
+    return TL_OK;
+}

@@ -113,4 +113,26 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
                     uint32_t stride, void* stream);
 
+// ---- batched chains (tl_batch.cu) ----
+struct BatchChain {
+    Geom g;
+    uint32_t* rows[2];          // two packed state buffers (ping-pong), each with pad rows
+    const int2* grange;
+    ThrView th;
+    DevRng rng;
+    uint32_t* sweep_base;       // device counter: absolute sweep of the next launch block
+};
+struct BatchTile {
+    int chain, lo, hi;          // owned rows [lo, hi) of chain `chain`
+};
+int batch_prepare(size_t smem_bytes, int* blocks_per_sm);
+int launch_batch(const BatchChain* chains, const BatchTile* tiles, int ntiles, int R, uint32_t sweep_off, int src,
+                 unsigned int* cursor, int grid, size_t smem_bytes, void* stream);
+// advance every chain's sweep counter by k and zero the launch cursors
+int launch_batch_advance(const BatchChain* chains, int nchains, uint32_t k, unsigned int* cursors, int ncursors,
+                         void* stream);
+int launch_batch_hash(const BatchChain* chains, const BatchTile* tiles, int ntiles, int buf,
+                      unsigned long long* out, void* stream);
+int launch_batch_copy(const BatchChain* chains, const BatchTile* tiles, int ntiles, int from, void* stream);
+
 }  // namespace tl
