@@ -322,6 +322,94 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 4096 Aztec chains, orders U{16..512} (seed 3), per-site
+# heat-bath thresholds from log-normal (sigma 0.5) dual-edge weights, 10^4
+# sweeps per step in CUDA-graph blocks of 100; compared with one launch per
+# chain per R sweeps on the same GPU.
+# ---------------------------------------------------------------------------
+BATCH_CHAINS, BATCH_SWEEPS, BATCH_BLOCK = 4096, 10_000, 100
+
+
+def build_batch(T, ctx, nchains):
+    import numpy as np
+    orders = np.random.default_rng(3).integers(16, 513, size=nchains)
+    chains, sites, edges = [], 0, 0
+    for i, n in enumerate(orders):
+        dom = T.Domain.aztec(int(n))
+        W = 2 * int(n) + 1
+        z = np.random.default_rng([3, i]).standard_normal((2, W, W))
+        t = dom.domino_thresholds(np.exp(0.5 * z))
+        chains.append(T.Chain(ctx, dom, seed=3, stream_id=i, th=T.thresholds(site=t)))
+        sites += dom.info.sites
+        edges += dom.info.edges
+    return chains, orders, sites, edges
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import paper_1804_07250_gb300 as T
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = T.Context(local)
+    t0 = time.perf_counter()
+    chains, orders, sites, edges = build_batch(T, ctx, args.chains)
+    setup_s = time.perf_counter() - t0
+    b = T.Batch(ctx, chains)
+    stream = torch.cuda.Stream()
+    plan = b.autotune(trial_sweeps=8, stream=stream)
+    b.set_plan(graph_block=BATCH_BLOCK)
+    for _ in range(args.warmup):
+        b.run(BATCH_BLOCK, stream=stream)
+    stream.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = b.launches
+    total_ms, step_ms = 0.0, []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(args.batch_sweeps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    total_ms = sum(step_ms)
+    clocks = sampler.stop()
+    launches = b.launches - l0
+    value = sites * args.batch_sweeps * args.steps / (total_ms / 1e3)
+    # one launch per chain per R sweeps, same kernel
+    kpc = 2 * plan["sweeps_per_launch"] * 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run_per_chain(kpc, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_chain = sites * kpc / (e0.elapsed_time(e1) / 1e3)
+    peak, peak_kind = peaks()
+    us_sweep = 1e3 * total_ms / (args.steps * args.batch_sweeps)
+    state_bytes = 2 * edges / 8
+    line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batched_%d_aztec_chains_n16_512_lognormal" % args.chains,
+                       "chains": args.chains, "sites_per_sweep": int(sites),
+                       "mean_n2": float(np.mean(orders.astype(np.float64) ** 2)),
+                       "sweeps_per_step": args.batch_sweeps, "graph_block": BATCH_BLOCK,
+                       "plan": b.plan(), "autotuned": plan, "setup_s": setup_s,
+                       "l2": "state (%.0f MB) larger than L2" % (sum(c.domain.info.packed_bytes for c in chains) / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": state_bytes / (us_sweep * 1e-6) / 1e9, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": state_bytes / (us_sweep * 1e-6) / 1e9 / peak,
+                         "frac_state_plus_thresholds": (state_bytes + 4 * sites) / (us_sweep * 1e-6) / 1e9 / peak,
+                         "us_per_sweep": us_sweep, "traffic": None, "kernel": "batch_kernel"},
+            "batched_vs_per_chain": {"batched": value, "per_chain": per_chain, "speedup": value / per_chain,
+                                     "per_chain_sweeps": kpc},
+            "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,7 +421,13 @@ def main():
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["aztec2048", "batch"], default="aztec2048")
+    ap.add_argument("--chains", type=int, default=BATCH_CHAINS)
+    ap.add_argument("--batch-sweeps", type=int, default=BATCH_SWEEPS)
     args = ap.parse_args()
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
