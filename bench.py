@@ -410,6 +410,48 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Served workload: Poisson arrivals (mean 200 requests/s, seed 5) of sampling
+# jobs (a third each Aztec n in [32, 2048], hexagons with sides in [16, 512],
+# six-vertex domain wall N in [32, 1024]; uniform or log-normal weights;
+# 10^3..10^5 sweeps log-uniform), admitted against an 80 GB budget.
+# ---------------------------------------------------------------------------
+def run_serve(args):
+    import numpy as np
+    import torch
+    import paper_1804_07250_gb300 as T
+    from paper_1804_07250_gb300 import serve
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = T.Context(local)
+    out = {}
+    for label, rate in (("rate", args.rate), ("half_rate", args.rate / 2)):
+        reqs = serve.make_requests(args.requests, rate=rate, seed=5)
+        srv = serve.Server(ctx, budget_bytes=int(args.budget_gb * 1e9))
+        sampler = ClockSampler(local)
+        sampler.start()
+        done, stats = srv.run(reqs, keep_chains=False)
+        stats["clocks"] = sampler.stop()
+        stats["offered_attempts_per_s"] = float(sum(
+            r.sweeps * (T.Domain.aztec(*r.size).info.sites if r.kind == "aztec" else
+                        T.Domain.hexagon(*r.size).info.sites if r.kind == "hexagon" else
+                        (r.size[0] - 1) ** 2) for r in reqs) / reqs[-1].arrival)
+        out[label] = {"rate_per_s": rate, **stats}
+        if label == "rate":
+            rng = np.random.default_rng(11)
+            pick = rng.choice(len(done), size=min(args.check, len(done)), replace=False)
+            same = sum(int(done[i].result_hash == serve.alone_hash(ctx, done[i].req)) for i in pick)
+            out["alone_vs_mixed"] = {"checked": int(len(pick)), "identical": int(same)}
+    main_stats = out["rate"]
+    line = {"metric": METRIC, "value": main_stats["attempts_per_s"], "unit": "attempts/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * main_stats["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "served_poisson_%g_per_s_%d_requests" % (args.rate, args.requests),
+                       "budget_gb": args.budget_gb, "block": 100},
+            "serve": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,12 +463,19 @@ def main():
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["aztec2048", "batch"], default="aztec2048")
+    ap.add_argument("--workload", choices=["aztec2048", "batch", "serve"], default="aztec2048")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=80.0)
+    ap.add_argument("--check", type=int, default=50)
     ap.add_argument("--chains", type=int, default=BATCH_CHAINS)
     ap.add_argument("--batch-sweeps", type=int, default=BATCH_SWEEPS)
     args = ap.parse_args()
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
+        return
+    if args.workload == "serve" and args.impl == "ours":
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

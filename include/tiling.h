@@ -165,6 +165,17 @@ int tl_domain_initial_state(const tl_domain* d, uint8_t* canon, size_t cap);
 int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w, size_t n_w,
                                       uint32_t* t, size_t n_t);
 
+/* Generated log-normal weights (weight = exp(sigma Z), Z standard normal),
+ * drawn on the device from Philox4x32-10 keyed by `seed` and the canonical
+ * index of each edge (dominoes: dual-edge weights, thresholds as in
+ * tl_thresholds_domino_edge_weights) or vertex (lozenges: volume weight q_v,
+ * P(add) = q_v / (1 + q_v)).  Writes t[H][W] into device memory `t_dev`
+ * (n_t >= W*H) on `stream`; the FP64 threshold arithmetic uses correctly
+ * rounded operations in the order given above.  For workloads whose weights
+ * are random, such as served sampling jobs.  Six-vertex: TL_EINVAL. */
+int tl_thresholds_lognormal_device(const tl_domain* d, double sigma, uint64_t seed, uint32_t* t_dev, size_t n_t,
+                                   void* stream);
+
 /* Lozenge q^volume (Sec. 1.1.1 volume weights on the cube picture, Sec.
  * 1.2.1): P(add a cube) = q / (1 + q); t_add as above, t_rem = 2^32 - t_add.
  * A flippable site ends with the cube present iff u < t_add.  TL_EINVAL if q
@@ -192,7 +203,7 @@ typedef enum {
 typedef struct {
     int kind;                 /* tl_threshold_kind */
     uint32_t scalar;          /* TL_T_SCALAR */
-    const uint32_t* site;     /* TL_T_SITE: host array [H][W] (t per vertex) */
+    const uint32_t* site;     /* TL_T_SITE: host or device array [H][W] (t per vertex) */
     uint32_t table16[16];     /* TL_T_TABLE16 */
 } tl_thresholds;
 
@@ -348,6 +359,11 @@ typedef struct {
 
 int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out);
 void tl_batch_destroy(tl_batch* b);
+/* Continuous batching: add a chain to / remove a chain from the batch
+ * between runs (the work list is re-planned; removal waits for the device). */
+int tl_batch_add(tl_batch* b, tl_chain* c);
+int tl_batch_remove(tl_batch* b, tl_chain* c);
+size_t tl_batch_size(const tl_batch* b);
 int tl_batch_run(tl_batch* b, uint64_t k, void* stream);
 /* The comparison point: the same kernel launched once per chain per R
  * sweeps (no batching, no graph). */

@@ -88,6 +88,7 @@ _SIG = {
     "tl_domain_initial_state": (_i, [_vp, _vp, ctypes.c_size_t]),
     "tl_thresholds_domino_edge_weights": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]),
     "tl_thresholds_lozenge_q": (_i, [ctypes.c_double, _vp, _vp]),
+    "tl_thresholds_lognormal_device": (_i, [_vp, ctypes.c_double, _u64, _vp, ctypes.c_size_t, _vp]),
     "tl_thresholds_6v": (_i, [_vp, _vp]),
     "tl_chain_create": (_i, [_vp, _vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds),
                              ctypes.POINTER(_vp)]),
@@ -115,6 +116,9 @@ _SIG = {
     "tl_batch_get_plan": (_i, [_vp, ctypes.POINTER(BatchPlan)]),
     "tl_batch_autotune": (_i, [_vp, _u64, _vp, ctypes.POINTER(BatchPlan)]),
     "tl_batch_launches": (_u64, [_vp]),
+    "tl_batch_add": (_i, [_vp, _vp]),
+    "tl_batch_remove": (_i, [_vp, _vp]),
+    "tl_batch_size": (ctypes.c_size_t, [_vp]),
     "tl_read_density": (_i, [_vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "tl_read_domino_nsew": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
 }
@@ -222,6 +226,12 @@ class Domain:
         _check(_lib.tl_thresholds_domino_edge_weights(self._h, pw, w.size, pt, t.size))
         return t
 
+    def lognormal_thresholds_device(self, sigma: float, seed: int, out, stream=None):
+        """Per-site thresholds from device-generated log-normal weights (device buffer)."""
+        p, n = _ptr(out)
+        _check(_lib.tl_thresholds_lognormal_device(self._h, sigma, seed, p, n // 4, _stream(stream)))
+        return out
+
     def close(self):
         if self._h:
             _lib.tl_domain_destroy(self._h)
@@ -256,8 +266,12 @@ def thresholds(scalar=None, site=None, table16=None) -> Thresholds:
             th.table16[i] = int(v)
     elif site is not None:
         th.kind = T_SITE
-        th._site = np.ascontiguousarray(site, dtype=np.uint32)
-        th.site = th._site.ctypes.data
+        if isinstance(site, np.ndarray):
+            th._site = np.ascontiguousarray(site, dtype=np.uint32)
+            th.site = th._site.ctypes.data
+        else:                                   # a device tensor
+            th._site = site
+            th.site, _ = _ptr(site)
     else:
         th.kind = T_SCALAR
         th.scalar = int(scalar if scalar is not None else 1 << 31)
@@ -386,13 +400,23 @@ class Chain:
 class Batch:
     """Many chains advanced together (one work list, CUDA-graph blocks)."""
 
-    def __init__(self, ctx: Context, chains):
+    def __init__(self, ctx: Context, chains=()):
         self.ctx, self.chains = ctx, list(chains)
-        arr = (_vp * len(self.chains))(*[c._h for c in self.chains])
-        self._arr = arr
+        arr = (_vp * max(1, len(self.chains)))(*[c._h for c in self.chains])
         h = _vp()
         _check(_lib.tl_batch_create(ctx._h, ctypes.cast(arr, _vp), len(self.chains), ctypes.byref(h)))
         self._h = h
+
+    def add(self, chain: Chain):
+        _check(_lib.tl_batch_add(self._h, chain._h))
+        self.chains.append(chain)
+
+    def remove(self, chain: Chain):
+        _check(_lib.tl_batch_remove(self._h, chain._h))
+        self.chains.remove(chain)
+
+    def __len__(self):
+        return int(_lib.tl_batch_size(self._h))
 
     def run(self, k: int, stream=None):
         _check(_lib.tl_batch_run(self._h, k, _stream(stream)))

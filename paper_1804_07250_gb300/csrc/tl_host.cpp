@@ -505,6 +505,18 @@ TL_API int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w
     return TL_OK;
 }
 
+TL_API int tl_thresholds_lognormal_device(const tl_domain* d, double sigma, uint64_t seed, uint32_t* t_dev,
+                                          size_t n_t, void* stream)
+{
+    if (!d || !t_dev || !(sigma >= 0.0) || !std::isfinite(sigma))
+        return fail(TL_EINVAL, "tl_thresholds_lognormal_device: bad argument");
+    if (d->g.lattice == LAT_SIXV) return fail(TL_EINVAL, "tl_thresholds_lognormal_device: six-vertex uses tl_thresholds_6v");
+    if (n_t < (size_t)d->g.W * d->g.H) return fail(TL_EINVAL, "tl_thresholds_lognormal_device: n_t too small");
+    const int e = launch_lognormal_thresholds(d->g.lattice, d->g.W, d->g.H, sigma, seed, t_dev, stream);
+    if (e) return fail(TL_ECUDA, "tl_thresholds_lognormal_device: %s", cudaGetErrorString((cudaError_t)e));
+    return TL_OK;
+}
+
 TL_API int tl_thresholds_lozenge_q(double q, uint32_t* t_add, uint32_t* t_rem)
 {
     if (!t_add || !t_rem || !(q > 0.0) || !std::isfinite(q)) return fail(TL_EINVAL, "lozenge thresholds: bad q");
@@ -723,7 +735,8 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
             chain_free(c);
             return rc;
         }
-        e = cudaMemcpy(tdev, th->site, sizeof(uint32_t) * g.W * g.H, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(tdev, th->site, sizeof(uint32_t) * g.W * g.H,
+                       is_device_ptr(th->site) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = (cudaError_t)launch_threshold_planes(g, tdev, c->tplanes, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(tdev);
@@ -1286,7 +1299,8 @@ struct tl_batch {
     BatchChain* d_chains = nullptr;
     std::vector<uint32_t*> alt;           // second state buffer of every chain
     uint32_t* d_sweep = nullptr;          // per-chain sweep counters on the device
-    std::vector<uint32_t> h_sweep;
+    uint32_t* h_sweep = nullptr;          // pinned staging for the counters
+    size_t cap = 0;                       // capacity of the descriptor arrays
     std::vector<BatchTile> tiles_lpt;     // largest first (batched launches)
     std::vector<BatchTile> tiles_chain;   // grouped by chain (per-chain launches)
     std::vector<int> chain_first;         // first tile of each chain in tiles_chain
@@ -1301,7 +1315,7 @@ struct tl_batch {
     int src = 0;                          // buffer holding the current state
     uint64_t launches = 0;
     cudaGraphExec_t graph = nullptr;
-    int graph_block = 0;
+    int graph_block = 0, graph_R = 0, graph_launches = 0;
 };
 
 static void batch_free_plan(tl_batch* b)
@@ -1320,6 +1334,7 @@ static void batch_free(tl_batch* b)
     for (auto* p : b->alt) cudaFree(p);
     cudaFree(b->d_chains);
     cudaFree(b->d_sweep);
+    cudaFreeHost(b->h_sweep);
     cudaFree(b->d_cursor);
     cudaFree(b->d_hash);
     delete b;
@@ -1376,51 +1391,80 @@ static int batch_plan(tl_batch* b, int tile_rows, int R)
     return TL_OK;
 }
 
-TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out)
+// (Re)build the device descriptors of every chain in the batch.
+static int batch_rebuild(tl_batch* b)
 {
-    if (!ctx || !chains || !out || n == 0) return fail(TL_EINVAL, "tl_batch_create: bad argument");
-    CUDA_TRY(cudaSetDevice(ctx->device));
-    tl_batch* b = new (std::nothrow) tl_batch();
-    if (!b) return fail(TL_ENOMEM, "tl_batch_create: host allocation");
-    b->ctx = ctx;
-    int rc = TL_OK;
-    for (size_t i = 0; i < n && rc == TL_OK; ++i) {
-        tl_chain* c = chains[i];
-        if (!c || c->ctx->device != ctx->device) rc = fail(TL_EINVAL, "tl_batch_create: chain %zu invalid", i);
-        else if (c->density_on) rc = fail(TL_EINVAL, "tl_batch_create: chain %zu samples densities", i);
-        b->chains.push_back(c);
-    }
-    const int nc = (int)n;
-    b->ncursor = 1024;
-    if (rc == TL_OK && ((rc = dev_alloc(&b->d_chains, n, "batch chains")) || (rc = dev_alloc(&b->d_sweep, n, "sweeps")) ||
-                        (rc = dev_alloc(&b->d_cursor, (size_t)b->ncursor, "cursors")) ||
-                        (rc = dev_alloc(&b->d_hash, n, "hashes")))) {
-    }
-    for (int i = 0; i < nc && rc == TL_OK; ++i) {
-        tl_chain* c = b->chains[i];
-        uint32_t* a = nullptr;
-        rc = dev_alloc(&a, (size_t)c->g.total_words, "second state buffer");
-        if (rc == TL_OK) {
-            b->alt.push_back(a);
-            if (cudaMemset(a, 0, (size_t)c->g.total_words * 4) != cudaSuccess)
-                rc = fail(TL_ECUDA, "tl_batch_create: memset");
+    const size_t n = b->chains.size();
+    if (n > b->cap) {
+        const size_t cap = std::max<size_t>(n, 2 * b->cap);
+        cudaFree(b->d_chains);
+        cudaFree(b->d_sweep);
+        cudaFree(b->d_hash);
+        cudaFreeHost(b->h_sweep);
+        b->d_chains = nullptr;
+        b->d_sweep = nullptr;
+        b->d_hash = nullptr;
+        b->h_sweep = nullptr;
+        TL_TRY(dev_alloc(&b->d_chains, cap, "batch chains"));
+        TL_TRY(dev_alloc(&b->d_sweep, cap, "sweeps"));
+        TL_TRY(dev_alloc(&b->d_hash, cap, "hashes"));
+        if (cudaMallocHost((void**)&b->h_sweep, cap * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TL_ENOMEM, "batch: pinned host allocation");
         }
+        b->cap = cap;
+    }
+    b->hchains.clear();
+    for (size_t i = 0; i < n; ++i) {
+        tl_chain* c = b->chains[i];
         BatchChain bc{};
         bc.g = c->g;
         bc.rows[0] = c->rows;
-        bc.rows[1] = a;
+        bc.rows[1] = b->alt[i];
         bc.grange = c->grange;
         bc.th = c->th;
         bc.rng = c->rng;
         bc.sweep_base = b->d_sweep + i;
         b->hchains.push_back(bc);
-        b->h_sweep.push_back((uint32_t)c->sweep);
     }
-    if (rc == TL_OK && cudaMemcpy(b->d_chains, b->hchains.data(), sizeof(BatchChain) * n, cudaMemcpyHostToDevice) != cudaSuccess)
-        rc = fail(TL_ECUDA, "tl_batch_create: upload");
+    if (n) CUDA_TRY(cudaMemcpy(b->d_chains, b->hchains.data(), sizeof(BatchChain) * n, cudaMemcpyHostToDevice));
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (n) return batch_plan(b, b->tile_rows, b->R);
+    b->ntiles = 0;
+    return TL_OK;
+}
+
+static int batch_attach(tl_batch* b, tl_chain* c)
+{
+    if (!c || c->ctx->device != b->ctx->device) return fail(TL_EINVAL, "batch: chain on another device");
+    if (c->density_on) return fail(TL_EINVAL, "batch: chain samples densities");
+    for (auto* x : b->chains)
+        if (x == c) return fail(TL_EINVAL, "batch: chain already in the batch");
+    uint32_t* a = nullptr;
+    TL_TRY(dev_alloc(&a, (size_t)c->g.total_words, "second state buffer"));
+    if (cudaMemset(a, 0, (size_t)c->g.total_words * 4) != cudaSuccess) {
+        cudaFree(a);
+        return fail(TL_ECUDA, "batch: memset");
+    }
+    b->chains.push_back(c);
+    b->alt.push_back(a);
+    return TL_OK;
+}
+
+TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out)
+{
+    if (!ctx || !out || (n && !chains)) return fail(TL_EINVAL, "tl_batch_create: bad argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    tl_batch* b = new (std::nothrow) tl_batch();
+    if (!b) return fail(TL_ENOMEM, "tl_batch_create: host allocation");
+    b->ctx = ctx;
+    b->ncursor = 1024;
+    int rc = dev_alloc(&b->d_cursor, (size_t)b->ncursor, "cursors");
     if (rc == TL_OK && cudaMemset(b->d_cursor, 0, sizeof(unsigned int) * b->ncursor) != cudaSuccess)
         rc = fail(TL_ECUDA, "tl_batch_create: memset");
-    if (rc == TL_OK) rc = batch_plan(b, 64, 2);
+    for (size_t i = 0; i < n && rc == TL_OK; ++i) rc = batch_attach(b, chains[i]);
+    if (rc == TL_OK) rc = batch_rebuild(b);
     if (rc != TL_OK) {
         batch_free(b);
         return rc;
@@ -1428,6 +1472,30 @@ TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_ba
     *out = b;
     return TL_OK;
 }
+
+TL_API int tl_batch_add(tl_batch* b, tl_chain* c)
+{
+    if (!b) return fail(TL_EINVAL, "tl_batch_add: NULL batch");
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    TL_TRY(batch_attach(b, c));
+    return batch_rebuild(b);
+}
+
+TL_API int tl_batch_remove(tl_batch* b, tl_chain* c)
+{
+    if (!b || !c) return fail(TL_EINVAL, "tl_batch_remove: NULL argument");
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    size_t i = 0;
+    while (i < b->chains.size() && b->chains[i] != c) ++i;
+    if (i == b->chains.size()) return fail(TL_EINVAL, "tl_batch_remove: chain not in the batch");
+    CUDA_TRY(cudaDeviceSynchronize());   // no launch may still use its second buffer
+    cudaFree(b->alt[i]);
+    b->chains.erase(b->chains.begin() + (long)i);
+    b->alt.erase(b->alt.begin() + (long)i);
+    return batch_rebuild(b);
+}
+
+TL_API size_t tl_batch_size(const tl_batch* b) { return b ? b->chains.size() : 0; }
 
 TL_API void tl_batch_destroy(tl_batch* b)
 {
@@ -1437,14 +1505,15 @@ TL_API void tl_batch_destroy(tl_batch* b)
 
 TL_API uint64_t tl_batch_launches(const tl_batch* b) { return b ? b->launches : 0; }
 
-static int batch_upload_sweeps(tl_batch* b, void* stream)
+static int batch_upload_sweeps(tl_batch* b, uint64_t k, void* stream)
 {
+    // the pinned staging buffer may still feed the previous run's copy
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));
     for (size_t i = 0; i < b->chains.size(); ++i) {
-        if (b->chains[i]->sweep + 1 > 0xFFFFFFFFull) return fail(TL_EINVAL, "batch: sweep index beyond 2^32");
+        if (b->chains[i]->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "batch: sweep index beyond 2^32");
         b->h_sweep[i] = (uint32_t)b->chains[i]->sweep;
     }
-    CUDA_TRY(cudaMemcpyAsync(b->d_sweep, b->h_sweep.data(), 4 * b->h_sweep.size(), cudaMemcpyHostToDevice, SS(stream)));
-    CUDA_TRY(cudaStreamSynchronize(SS(stream)));   // the host vector is pageable
+    CUDA_TRY(cudaMemcpyAsync(b->d_sweep, b->h_sweep, 4 * b->chains.size(), cudaMemcpyHostToDevice, SS(stream)));
     return TL_OK;
 }
 
@@ -1485,20 +1554,45 @@ static int batch_finish(tl_batch* b, uint64_t k, void* stream)
     return TL_OK;
 }
 
+// Launch sizes covering `k` sweeps with at most R sweeps each and an even
+// number of launches, so that the state ends in the buffer it started in.
+static std::vector<int> batch_launch_sizes(uint64_t k, int R)
+{
+    std::vector<int> v;
+    for (uint64_t d = 0; d < k; d += (uint64_t)R) v.push_back((int)std::min<uint64_t>((uint64_t)R, k - d));
+    if (v.size() % 2) {
+        // split the largest launch in two (a launch of one sweep cannot be split)
+        size_t i = 0;
+        for (size_t j = 0; j < v.size(); ++j)
+            if (v[j] > v[i]) i = j;
+        if (v[i] >= 2) {
+            const int a = v[i] / 2;
+            v[i] -= a;
+            v.insert(v.begin() + (long)i + 1, a);
+        }
+    }
+    return v;
+}
+
 // Graph of one block of `block` sweeps: the launches plus the counter advance.
 static int batch_build_graph(tl_batch* b, void* stream)
 {
-    if (b->graph && b->graph_block == b->block) return TL_OK;
+    if (b->graph && b->graph_block == b->block && b->graph_R == b->R) return TL_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     cudaStream_t s = SS(stream);
     if (!s) return TL_OK;   // the legacy stream cannot be captured: run without a graph
-    const int nl = b->block / b->R;
+    const std::vector<int> sizes = batch_launch_sizes((uint64_t)b->block, b->R);
+    if (sizes.size() % 2) return TL_OK;   // cannot keep the buffers aligned: no graph
     const int src0 = b->src;
     const uint64_t l0 = b->launches;
     CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int rc = TL_OK;
-    for (int j = 0; j < nl && rc == TL_OK; ++j) rc = batch_launch(b, b->R, (uint32_t)(j * b->R), j, stream, false);
+    uint32_t off = 0;
+    for (size_t j = 0; j < sizes.size() && rc == TL_OK; ++j) {
+        rc = batch_launch(b, sizes[j], off, (int)j, stream, false);
+        off += (uint32_t)sizes[j];
+    }
     if (rc == TL_OK) {
         const int e = launch_batch_advance(b->d_chains, (int)b->chains.size(), (uint32_t)b->block, b->d_cursor, 0, stream);
         if (e) rc = fail(TL_ECUDA, "batch advance: %s", cudaGetErrorString((cudaError_t)e));
@@ -1516,30 +1610,30 @@ static int batch_build_graph(tl_batch* b, void* stream)
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return fail(TL_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(ie));
     b->graph_block = b->block;
+    b->graph_R = b->R;
+    b->graph_launches = (int)sizes.size();
     return TL_OK;
 }
 
 static int batch_run(tl_batch* b, uint64_t k, void* stream, bool per_chain)
 {
     CUDA_TRY(cudaSetDevice(b->ctx->device));
-    if (k == 0) return TL_OK;
-    TL_TRY(batch_upload_sweeps(b, stream));
+    if (k == 0 || b->chains.empty()) return TL_OK;
+    TL_TRY(batch_upload_sweeps(b, k, stream));
     uint64_t done = 0;
-    int slot = 0;
-    // whole graph blocks (an even number of launches, so the state ends where it began)
-    const bool use_graph = !per_chain && b->block % b->R == 0 && (b->block / b->R) % 2 == 0;
-    if (use_graph && k >= (uint64_t)b->block) TL_TRY(batch_build_graph(b, stream));
-    while (use_graph && b->graph && k - done >= (uint64_t)b->block) {
+    if (!per_chain && k >= (uint64_t)b->block) TL_TRY(batch_build_graph(b, stream));
+    while (!per_chain && b->graph && k - done >= (uint64_t)b->block) {
         CUDA_TRY(cudaGraphLaunch(b->graph, SS(stream)));
-        b->launches += (uint64_t)(b->block / b->R) + 1;
+        b->launches += (uint64_t)b->graph_launches + 1;
         done += (uint64_t)b->block;
     }
-    // the rest: sweeps `done` onwards relative to the counters at the last advance
+    // the rest: offsets relative to the counters after the last advance
     const uint64_t rest_start = done;
-    while (done < k) {
-        const int r = (int)std::min<uint64_t>((uint64_t)b->R, k - done);
-        TL_TRY(batch_launch(b, r, (uint32_t)(done - rest_start), slot++, stream, per_chain));
-        done += (uint64_t)r;
+    const std::vector<int> sizes = batch_launch_sizes(k - done, b->R);
+    uint32_t off = 0;
+    for (size_t j = 0; j < sizes.size(); ++j) {
+        TL_TRY(batch_launch(b, sizes[j], off, (int)j, stream, per_chain));
+        off += (uint32_t)sizes[j];
     }
     if (k > rest_start) {
         const int e = launch_batch_advance(b->d_chains, (int)b->chains.size(), (uint32_t)(k - rest_start), b->d_cursor,

@@ -75,6 +75,8 @@ int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int
                   void* stream);
 int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t* planes,
                             void* stream);
+// Device-generated log-normal weights -> per-site thresholds [H][W].
+int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_t seed, uint32_t* t, void* stream);
 // Height with its row-offset scratch in a static device array (no allocation).
 int noalloc_height_max_rows();
 int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,

@@ -401,6 +401,71 @@ int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int
 }
 
 // ---------------------------------------------------------------------------
+// Generated log-normal weights and their heat-bath thresholds, on the device.
+// Weight of item i (an edge or a vertex, by canonical index) = exp(sigma Z),
+// Z standard normal by the Box-Muller transform of two 32-bit words of
+// Philox4x32-10(key = seed, counter = (i lo, i hi, 0x6C6F676E, 0)).  The
+// threshold arithmetic uses correctly rounded FP64 operations in the order of
+// the host formulas (no fused multiply-add), so for equal weights it equals
+// the host result bit for bit.
+// ---------------------------------------------------------------------------
+TL_DEV double lognormal_weight(uint64_t i, double sigma, uint32_t k0, uint32_t k1)
+{
+    const uint4 o = philox10((uint32_t)i, (uint32_t)(i >> 32), 0x6C6F676Eu, 0u, k0, k1);
+    const double u1 = ((double)o.x + 1.0) * (1.0 / 4294967296.0);   // (0, 1]
+    const double u2 = (double)o.y * (1.0 / 4294967296.0);           // [0, 1)
+    const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    return exp(sigma * z);
+}
+
+TL_DEV uint32_t prob_threshold(double p)
+{
+    const double t = floor(__dmul_rn(p, 4294967296.0));
+    if (!(t > 0.0)) return 0u;
+    if (t >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)t;
+}
+
+// Dominoes: edge weights on the canonical [2][H][W] layout; t at every vertex
+// from up = wE * wW, down = wN * wS, P = up / (up + down) (1.0 off the box).
+__global__ void lognormal_domino_kernel(int W, int H, double sigma, uint32_t k0, uint32_t k1, uint32_t* t)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % W), y = (int)(v / W);
+        auto wt = [&](int type, int xx, int yy) -> double {
+            if (xx < 0 || yy < 0 || xx >= W || yy >= H) return 1.0;
+            return lognormal_weight(((uint64_t)type * H + yy) * W + xx, sigma, k0, k1);
+        };
+        const double up = __dmul_rn(wt(0, x, y), wt(0, x - 1, y));
+        const double down = __dmul_rn(wt(1, x, y), wt(1, x, y - 1));
+        t[v] = prob_threshold(__ddiv_rn(up, __dadd_rn(up, down)));
+    }
+}
+
+// Lozenges: volume weight q_v per vertex; P(add a cube) = q / (1 + q).
+__global__ void lognormal_lozenge_kernel(int W, int H, double sigma, uint32_t k0, uint32_t k1, uint32_t* t)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const double q = lognormal_weight((uint64_t)v, sigma, k0, k1);
+        t[v] = prob_threshold(__ddiv_rn(q, __dadd_rn(1.0, q)));
+    }
+}
+
+int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_t seed, uint32_t* t, void* stream)
+{
+    const int64_t n = (int64_t)W * H;
+    if (lattice == LAT_DOMINO)
+        lognormal_domino_kernel<<<grid_for(n, 256), 256, 0, S(stream)>>>(W, H, sigma, (uint32_t)seed,
+                                                                       (uint32_t)(seed >> 32), t);
+    else
+        lognormal_lozenge_kernel<<<grid_for(n, 256), 256, 0, S(stream)>>>(W, H, sigma, (uint32_t)seed,
+                                                                        (uint32_t)(seed >> 32), t);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Height function without any allocation.  For callers that cannot allocate
 // device memory at the time they need the heights (for example code running
 // under a memory budget that forbids cudaMalloc, or a real-time loop that
