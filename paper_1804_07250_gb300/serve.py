@@ -164,6 +164,7 @@ class Server:
         attempts = 0
         busy = 0.0
         peak_active = 0
+        peak_in_use = 0
         n = len(requests)
         while len(finished) < n:
             while True:
@@ -184,6 +185,7 @@ class Server:
                 time.sleep(0.0005)
                 continue
             peak_active = max(peak_active, len(active))
+            peak_in_use = max(peak_in_use, in_use)
             k = min(self.block, min(j.remaining for j in active))
             ts = time.perf_counter()
             self.batch.run(k, stream=self.stream)
@@ -213,7 +215,8 @@ class Server:
         stats = {"requests": n, "wall_s": wall, "gpu_busy_s": busy, "attempts": attempts,
                  "attempts_per_s": attempts / wall, "attempts_per_busy_s": attempts / max(busy, 1e-9),
                  "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                 "mean_latency_s": float(lat.mean()), "peak_active": peak_active}
+                 "mean_latency_s": float(lat.mean()), "peak_active": peak_active,
+                 "peak_in_use_bytes": peak_in_use}
         return finished, stats
 
 
