@@ -351,7 +351,9 @@ typedef struct tl_batch tl_batch;
 typedef struct {
     int tile_rows;          /* rows per tile (0 = keep) */
     int sweeps_per_launch;  /* R (0 = keep) */
-    int graph_block;        /* sweeps per CUDA-graph block (0 = keep; default 100) */
+    int graph_block;        /* sweeps per CUDA-graph block (0 = keep; default 100;
+                               -1 = never capture graphs, e.g. while other threads
+                               use the legacy stream) */
     int grid;               /* out: CTAs per launch */
     int smem_bytes;         /* out: dynamic shared memory per CTA */
     int ntiles;             /* out: tiles in the work list */

@@ -1316,6 +1316,7 @@ struct tl_batch {
     uint64_t launches = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_block = 0, graph_R = 0, graph_launches = 0;
+    bool no_graph = false;
 };
 
 static void batch_free_plan(tl_batch* b)
@@ -1621,8 +1622,8 @@ static int batch_run(tl_batch* b, uint64_t k, void* stream, bool per_chain)
     if (k == 0 || b->chains.empty()) return TL_OK;
     TL_TRY(batch_upload_sweeps(b, k, stream));
     uint64_t done = 0;
-    if (!per_chain && k >= (uint64_t)b->block) TL_TRY(batch_build_graph(b, stream));
-    while (!per_chain && b->graph && k - done >= (uint64_t)b->block) {
+    if (!per_chain && !b->no_graph && k >= (uint64_t)b->block) TL_TRY(batch_build_graph(b, stream));
+    while (!per_chain && !b->no_graph && b->graph && k - done >= (uint64_t)b->block) {
         CUDA_TRY(cudaGraphLaunch(b->graph, SS(stream)));
         b->launches += (uint64_t)b->graph_launches + 1;
         done += (uint64_t)b->block;
@@ -1677,7 +1678,12 @@ TL_API int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* p)
     CUDA_TRY(cudaSetDevice(b->ctx->device));
     const int tr = p->tile_rows > 0 ? p->tile_rows : b->tile_rows;
     const int R = p->sweeps_per_launch > 0 ? p->sweeps_per_launch : b->R;
-    if (p->graph_block > 0) b->block = p->graph_block;
+    if (p->graph_block > 0) {
+        b->block = p->graph_block;
+        b->no_graph = false;
+    } else if (p->graph_block < 0) {
+        b->no_graph = true;
+    }
     CUDA_TRY(cudaDeviceSynchronize());
     return batch_plan(b, tr, R);
 }
@@ -1687,7 +1693,7 @@ TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
     if (!b || !p) return fail(TL_EINVAL, "tl_batch_get_plan: NULL argument");
     p->tile_rows = b->tile_rows;
     p->sweeps_per_launch = b->R;
-    p->graph_block = b->block;
+    p->graph_block = b->no_graph ? -1 : b->block;
     p->grid = b->grid;
     p->smem_bytes = (int)b->smem;
     p->ntiles = b->ntiles;

@@ -130,7 +130,9 @@ class Server:
         self.max_active = max_active
         self.stream = torch.cuda.Stream()
         self.batch = Batch(ctx)
-        self.batch.set_plan(tile_rows, sweeps_per_launch, block)
+        # membership changes between ticks and worker threads create chains
+        # meanwhile: plain launches, no graph capture
+        self.batch.set_plan(tile_rows, sweeps_per_launch, -1)
 
     def run(self, requests: list[Request], *, keep_chains: bool = False):
         """Serve `requests` in real time; returns the finished jobs and stats."""
