@@ -787,7 +787,7 @@ TL_API int tl_chain_set_plan(tl_chain* c, const tl_plan* p)
 {
     if (!c || !p || p->kernel < 0 || p->kernel > 2 || p->sweeps_per_launch < 0 || p->halo < 0 ||
         p->halo > 64 || (p->threads != 0 && p->threads != 512 && p->threads != 1024) || p->npre < 0 ||
-        p->npre > 4)
+        p->npre > 8)
         return fail(TL_EINVAL, "tl_chain_set_plan: bad plan");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     c->kernel = p->kernel;
@@ -873,8 +873,8 @@ static int default_halo(const Geom& g)
 }
 static int default_npre(const tl_chain* c)
 {
-    if (c->th.kind == THR_SCALAR) return c->th.kmax < 0 ? 1 : std::min(4, c->th.kmax + 1);
-    return c->g.lattice == LAT_DOMINO ? 2 : 4;
+    if (c->th.kind == THR_SCALAR) return c->th.kmax < 0 ? 1 : std::min(8, c->th.kmax + 1);
+    return 8;
 }
 
 // Local rows of stripe [lo, hi) of `C`, with halo h, clamped to the pads.

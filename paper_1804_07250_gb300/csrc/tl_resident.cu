@@ -245,9 +245,17 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 const uint32_t item = items[e.x + it];
                 const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                 const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                for (int k = 0; k < P.npre; ++k)
-                    rbuf[(size_t)k * cap + e.z + it] =
-                        philox10(grp, sweep, ((uint32_t)k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
+                // four planes at a time: independent chains the scheduler interleaves
+                for (int k0 = 0; k0 < P.npre; k0 += 4) {
+                    uint4 o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = philox10(grp, sweep, ((uint32_t)(k0 + q) << 16) | pass, P.rng.stream, P.rng.k0,
+                                        P.rng.k1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q < P.npre) rbuf[(size_t)(k0 + q) * cap + e.z + it] = o[q];
+                }
             }
         };
         if (!upd_role) gen(0);

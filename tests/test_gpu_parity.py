@@ -153,7 +153,7 @@ def test_resident_kernel_halos(T, ctx, kind, args, halo):
 
 
 @pytest.mark.parametrize("threads", [512, 1024])
-@pytest.mark.parametrize("npre", [1, 2, 4])
+@pytest.mark.parametrize("npre", [1, 2, 4, 8])
 @pytest.mark.parametrize("kind,args", [("aztec", (90,)), ("hex", (60, 70, 50)), ("dwbc", (150,))])
 def test_resident_kernel_threads_npre(T, ctx, kind, args, threads, npre):
     kw = dict(w6=SQ2) if kind == "dwbc" else dict(scalar=(1 << 31) if kind == "aztec" else 0x7FF80000)
