@@ -110,6 +110,39 @@ struct RndPre {
     TL_DEV uint4 operator()(int k) const { return k < npre ? pre[(size_t)k * stride] : more(k); }
 };
 
+// Same draw with the first `npre` planes read from shared memory: two loops,
+// so the on-the-spot Philox of later planes is never evaluated for the
+// planes that were generated ahead.
+template <class TB>
+TL_DEV uint4 heat_bath(uint4 f, int kmax, const RndPre& rnd, const TB& tb)
+{
+    uint4 und = f;
+    uint4 lt = make_uint4(0u, 0u, 0u, 0u);
+    const int kp = (kmax + 1) < rnd.npre ? (kmax + 1) : rnd.npre;
+    int k = 0;
+    for (; k < kp; ++k) {
+        if (!any4(und)) return lt;
+        const uint4 o = rnd.pre[(size_t)k * rnd.stride];
+        const uint4 t = tb(k);
+        uint32_t d;
+        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
+        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
+        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
+        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+    }
+    for (; k <= kmax; ++k) {
+        if (!any4(und)) break;
+        const uint4 o = rnd.more(k);
+        const uint4 t = tb(k);
+        uint32_t d;
+        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
+        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
+        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
+        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+    }
+    return lt;
+}
+
 struct TbScalar {
     uint32_t t;
     TL_DEV uint4 operator()(int k) const
