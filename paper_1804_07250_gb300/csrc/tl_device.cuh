@@ -178,11 +178,29 @@ TL_DEV uint32_t lut16(uint32_t tl, uint32_t tr, uint32_t br, uint32_t bl, uint32
     const uint32_t z1 = (br & w[3]) | (~br & w[2]);
     return (bl & z1) | (~bl & z0);
 }
+// The same lookup from an expanded table: T[idx] is all ones where bit 31-k
+// of t16[idx] is set, else zero (16 words per plane), so each level of the
+// selection tree is one three-input bitwise select.
+TL_DEV uint32_t sel(uint32_t c, uint32_t a1, uint32_t a0) { return (c & a1) | (~c & a0); }
+TL_DEV uint32_t lut16_tab(uint32_t tl, uint32_t tr, uint32_t br, uint32_t bl, const uint32_t* T)
+{
+    const uint32_t v0 = sel(tl, T[1], T[0]), v1 = sel(tl, T[3], T[2]), v2 = sel(tl, T[5], T[4]),
+                   v3 = sel(tl, T[7], T[6]), v4 = sel(tl, T[9], T[8]), v5 = sel(tl, T[11], T[10]),
+                   v6 = sel(tl, T[13], T[12]), v7 = sel(tl, T[15], T[14]);
+    const uint32_t w0 = sel(tr, v1, v0), w1 = sel(tr, v3, v2), w2 = sel(tr, v5, v4), w3 = sel(tr, v7, v6);
+    return sel(bl, sel(br, w3, w2), sel(br, w1, w0));
+}
 struct TbTable {
     const uint32_t* tmask;
+    const uint32_t* ttab;   // expanded table [32][16] or nullptr
     uint4 tl, tr, br, bl;
     TL_DEV uint4 operator()(int k) const
     {
+        if (ttab) {
+            const uint32_t* T = ttab + 16 * k;
+            return make_uint4(lut16_tab(tl.x, tr.x, br.x, bl.x, T), lut16_tab(tl.y, tr.y, br.y, bl.y, T),
+                              lut16_tab(tl.z, tr.z, br.z, bl.z, T), lut16_tab(tl.w, tr.w, br.w, bl.w, T));
+        }
         const uint32_t tt = tmask[k];
         return make_uint4(lut16(tl.x, tr.x, br.x, bl.x, tt), lut16(tl.y, tr.y, br.y, bl.y, tt),
                           lut16(tl.z, tr.z, br.z, bl.z, tt), lut16(tl.w, tr.w, br.w, bl.w, tt));
@@ -392,7 +410,7 @@ TL_DEV int sixv_py(uint32_t pass) { return (pass == 1u || pass == 3u) ? 1 : 0; }
 
 template <class RND>
 TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, uint32_t pass,
-                        const RND& rnd, const ThrView& th)
+                        const RND& rnd, const ThrView& th, const uint32_t* ttab)
 {
     const int px = sixv_px(pass);
     const int k0 = m << 2;
@@ -430,7 +448,7 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
     f.x = TL_6V_F(x, 0); f.y = TL_6V_F(y, 1); f.z = TL_6V_F(z, 2); f.w = TL_6V_F(w, 3);
 #undef TL_6V_F
     if (!any4(f)) return;
-    TbTable tb{th.tmask, TL, TR, BR, BL};
+    TbTable tb{th.tmask, ttab, TL, TR, BR, BL};
     const uint4 lt = heat_bath(f, 31, rnd, tb);
     const uint4 fl = make_uint4(f.x & (lt.x ^ B.x), f.y & (lt.y ^ B.y), f.z & (lt.z ^ B.z),
                                 f.w & (lt.w ^ B.w));
@@ -444,13 +462,14 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
 
 
 // Dispatch one group update for lattice LAT.
+// `ttab`: expanded six-vertex table in shared memory, or nullptr.
 template <int LAT, int TK, class RND>
 TL_DEV void group_update(uint32_t* row, int64_t RW, const Geom& g, int y, int m, uint32_t pass,
-                         const RND& rnd, const ThrView& th)
+                         const RND& rnd, const ThrView& th, const uint32_t* ttab = nullptr)
 {
     if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
     else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
-    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th);
+    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th, ttab);
 }
 
 // splitmix64 output for state x (Steele, Lea & Flood 2014).

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     __shared__ int4 s_ptab[64];
     __shared__ uint32_t s_psweep[64];
     __shared__ uint32_t s_next_sweep, s_next_pass;
+    __shared__ uint32_t s_ttab[LAT == LAT_SIXV ? 32 * 16 : 1];   // expanded six-vertex table
     const Geom& g = P.g;
     const int64_t RW = g.row_words;
     const int c = blockIdx.x, C = gridDim.x;
@@ -163,6 +164,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     uint2* fitems = reinterpret_cast<uint2*>((reinterpret_cast<uintptr_t>(off + NTAB * (nloc + 1)) + 7) & ~(uintptr_t)7);
 
     copy_rows_from_global(sm, P.rows0 + (int64_t)slo * RW, (int64_t)nloc * RW, tid, NT);
+    if (LAT == LAT_SIXV)
+        for (int i = tid; i < 32 * 16; i += NT) s_ttab[i] = ((P.th.tmask[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
 
     // item tables: active groups of each local row (six-vertex: one table per
     // face-row parity), prefix offsets per table
@@ -291,7 +294,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                     const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
                     const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
-                    group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th);
+                    group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th,
+                                          LAT == LAT_SIXV ? s_ttab : nullptr);
                 }
             } else if (i + 1 < hc) {
                 gen(i + 1);
