@@ -1,9 +1,16 @@
 #!/usr/bin/env python
-"""Throughput benchmark: uniform domino tilings of the Aztec diamond of order
-2048 (8,384,513 flip attempts per sweep), all-horizontal start, seed 7,
-10^5 heat-bath sweeps per step with edge-density samples every 100 sweeps
-after a 5 x 10^4 burn-in, then the height function, the north/south/east/
-west densities and the state hash.
+"""Throughput benchmark of the colour-class heat-bath sampler.
+
+Default workload: uniform domino tilings of the Aztec diamond of order 2048
+(8,384,513 flip attempts per sweep), all-horizontal start, seed 7, 10^5
+heat-bath sweeps per step with edge-density samples every 100 sweeps after a
+5 x 10^4 burn-in, then the height function, the north/south/east/west
+densities and the state hash.  Other single-chain workloads (--workload):
+aztec32 (order 32, 10^4 sweeps, seed 1), hexagon1024 (lozenge tilings of the
+1024 x 1024 x 1024 hexagon at q = 0.9995, 5 x 10^4 sweeps, seed 11) and
+dwbc2048 (six-vertex N = 2048 with domain-wall boundary at a = b = 1,
+c = sqrt 2, 5 x 10^4 sweeps, seed 11); plus batch (4096 chains) and serve
+(Poisson request stream).
 
 Metric: flip attempts per second (whole job, all ranks), with the dominant
 kernel's achieved fraction of the HBM roofline.  One process per GPU; for
@@ -11,6 +18,7 @@ N > 1 (torchrun) every rank runs an independent replica of the workload
 (weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload aztec2048|aztec32|hexagon1024|dwbc2048|batch|serve]
 
 --impl reference times the CPU oracle (the plain single-threaded reference
 sampler) on a bounded sample of the same workload on the host cores.
@@ -29,14 +37,25 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_ORDER = 2048
-SEED = 7
-SWEEPS = 100_000
-STRIDE = 100
-BURN = 50_000
-UNIFORM_T = 1 << 31
-WORKLOAD = "aztec_diamond_n2048_uniform_domino"
 METRIC = "flip attempts/s"
+SQRT2 = 2.0 ** 0.5
+
+
+# Single-chain workloads: domain, weights, seed and sweeps per step.
+# `oracle_sweeps` bounds the CPU oracle's sample per reference-arm step and
+# `baseline_sweeps` the cpu_baseline sample (about 10-30 s of CPU work).
+WORKLOADS = {
+    "aztec2048": dict(name="aztec_diamond_n2048_uniform_domino", kind="aztec", size=(2048,), seed=7,
+                      sweeps=100_000, density=(100, 50_000), oracle_sweeps=16, baseline_sweeps=100),
+    "aztec32": dict(name="aztec_diamond_n32_uniform_domino", kind="aztec", size=(32,), seed=1,
+                    sweeps=10_000, density=None, oracle_sweeps=10_000, baseline_sweeps=10_000),
+    "hexagon1024": dict(name="hexagon_1024x1024x1024_q0.9995_lozenge", kind="hexagon", size=(1024, 1024, 1024),
+                        seed=11, sweeps=50_000, q=0.9995, density=None, oracle_sweeps=32, baseline_sweeps=100),
+    "dwbc2048": dict(name="sixvertex_dwbc_n2048_a1_b1_c_sqrt2", kind="dwbc", size=(2048,), seed=11,
+                     sweeps=50_000, w6=(1.0, 1.0, 1.0, 1.0, SQRT2, SQRT2), density=None,
+                     oracle_sweeps=16, baseline_sweeps=60),
+}
+UNIFORM_T = 1 << 31
 KERNEL_SOURCES = ["paper_1804_07250_gb300/csrc/tl_resident.cu", "paper_1804_07250_gb300/csrc/tl_device.cuh"]
 
 
@@ -60,8 +79,6 @@ def recorded_traffic(workload):
     if not rec or rec.get("kernel_hash") != kernel_hash():
         return None
     return rec.get("dram_bytes_per_launch")
-ORACLE_SAMPLE_SWEEPS = 4     # per reference-arm step (bounded CPU sample)
-BASELINE_SAMPLE_SWEEPS = 40  # cpu_baseline sample: about 10-30 s of CPU work
 
 
 def peaks():
@@ -132,14 +149,43 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(sweeps: int):
+def oracle_setup(wl):
+    """Starting state and threshold keywords of a workload, from the oracle."""
     import oracle as O
-    st = O.aztec(N_ORDER)
-    sites = N_ORDER * N_ORDER + (N_ORDER - 1) ** 2
+    if wl["kind"] == "aztec":
+        return O.DOMINO, O.aztec(*wl["size"]), {"t_scalar": UNIFORM_T}
+    if wl["kind"] == "hexagon":
+        t_add, _ = O.lozenge_thresholds(wl["q"])
+        return O.LOZENGE, O.hexagon(*wl["size"]), {"t_scalar": t_add}
+    return O.SIXV, O.dwbc(*wl["size"]), {"t16": O.sixv_thresholds(wl["w6"])}
+
+
+def oracle_rate(wl, sweeps: int, sites: int, state=None):
+    """Attempts/s of the oracle over `sweeps` sweeps; continues from `state`
+    (lattice, array, sweep0) when given so that repeated samples do not all
+    time the first sweeps after the start."""
+    import oracle as O
+    if state is None:
+        lat, st, kw = oracle_setup(wl)
+        state = [lat, st, kw, 0]
+    lat, st, kw, s0 = state
     t0 = time.perf_counter()
-    O.sweeps(O.DOMINO, st, seed=SEED, stream=0, sweep0=0, k=sweeps, t_scalar=UNIFORM_T)
+    O.sweeps(lat, st, seed=wl["seed"], stream=0, sweep0=s0, k=sweeps, **kw)
     dt = time.perf_counter() - t0
-    return sites * sweeps / dt, dt
+    state[3] = s0 + sweeps
+    return sites * sweeps / dt, dt, state
+
+
+def workload_sites(wl):
+    """Interior sites: Aztec n^2 + (n-1)^2, six-vertex (N-1)^2, hexagon
+    ab + bc + ca - a - b - c + 1."""
+    if wl["kind"] == "aztec":
+        n = wl["size"][0]
+        return n * n + (n - 1) ** 2
+    if wl["kind"] == "dwbc":
+        return (wl["size"][0] - 1) ** 2
+    a, b, c = wl["size"]
+    return a * b + b * c + c * a - a - b - c + 1
 
 
 def run_reference(args):
@@ -148,21 +194,24 @@ def run_reference(args):
         return
     import oracle as O
     O.build()
+    wl = WORKLOADS[args.workload]
+    sites = workload_sites(wl)
+    k = wl["oracle_sweeps"]
+    state = None
     for _ in range(args.warmup):
-        oracle_rate(1)
-    rates, total = [], 0.0
+        _, _, state = oracle_rate(wl, 1, sites, state)
+    total = 0.0
     for _ in range(args.steps):
-        r, dt = oracle_rate(ORACLE_SAMPLE_SWEEPS)
-        rates.append(r)
+        _, dt, state = oracle_rate(wl, k, sites, state)
         total += dt
-    value = args.steps * ORACLE_SAMPLE_SWEEPS * (N_ORDER * N_ORDER + (N_ORDER - 1) ** 2) / total
-    sample = "%d sweeps per step of the %s workload (of %d)" % (ORACLE_SAMPLE_SWEEPS, WORKLOAD, SWEEPS)
+    value = args.steps * k * sites / total
+    sample = "%d sweeps per step of the %s workload (of %d)" % (k, wl["name"], wl["sweeps"])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_ORDER, "sweeps_per_step": ORACLE_SAMPLE_SWEEPS,
-                       "seed": SEED},
+            "config": {"workload": wl["name"], "size": list(wl["size"]), "sweeps_per_step": k,
+                       "seed": wl["seed"]},
             "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0,
@@ -190,29 +239,48 @@ def run_ours(args):
 
     import paper_1804_07250_gb300 as T
 
+    wl = WORKLOADS[args.workload]
+    SWEEPS = wl["sweeps"]
     ctx = T.Context(local)
-    dom = T.Domain.aztec(N_ORDER)
+    if wl["kind"] == "aztec":
+        dom = T.Domain.aztec(*wl["size"])
+        th = T.thresholds(scalar=UNIFORM_T)
+        thr_desc = UNIFORM_T
+    elif wl["kind"] == "hexagon":
+        dom = T.Domain.hexagon(*wl["size"])
+        t_add, _ = T.lozenge_thresholds(wl["q"])
+        th = T.thresholds(scalar=t_add)
+        thr_desc = {"q": wl["q"], "t_add": t_add}
+    else:
+        dom = T.Domain.dwbc(*wl["size"])
+        t16 = T.sixv_thresholds(wl["w6"])
+        th = T.thresholds(table16=t16)
+        thr_desc = {"w6": list(wl["w6"]), "t16": [int(v) for v in t16]}
     info = dom.info
     stream = torch.cuda.Stream()
-    chain = T.Chain(ctx, dom, seed=SEED, stream_id=0, th=T.thresholds(scalar=UNIFORM_T))
+    chain = T.Chain(ctx, dom, seed=wl["seed"], stream_id=0, th=th)
     if args.kernel or args.spl or args.halo or args.threads:
         chain.set_plan(args.kernel, args.spl, args.halo, args.threads)
-    H, W = info.height, info.width
-    height_dev = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    nsew_dev = torch.empty((4, H - 1, W - 1), dtype=torch.float64, device="cuda")
+    hshape = dom.height_shape
+    density = wl["density"]
+    height_dev = torch.empty(hshape, dtype=torch.int32, device="cuda")
+    nsew_dev = (torch.empty((4, info.height - 1, info.width - 1), dtype=torch.float64, device="cuda")
+                if density else None)
     hash_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
     def step(s, ev=None):
         chain.reset(stream=s)
-        chain.density_begin(STRIDE, BURN)
+        if density:
+            chain.density_begin(*density)
         if ev:
             ev[0].record(s)
         chain.run(SWEEPS, stream=s)
         if ev:
             ev[1].record(s)
         chain.read_height(height_dev, stream=s)
-        chain.read_nsew(nsew_dev, stream=s)
+        if density:
+            chain.read_nsew(nsew_dev, stream=s)
         chain.state_hash(out=hash_dev, stream=s)
 
     for _ in range(args.warmup):
@@ -231,7 +299,6 @@ def run_ours(args):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = chain.launches
         e0.record(stream)
         step(stream, (r0, r1))
         e1.record(stream)
@@ -252,22 +319,30 @@ def run_ours(args):
     attempts_step = info.sites * SWEEPS
     value = world * attempts_step * args.steps / (total_ms / 1e3)
 
-    # dominant kernel: the sweep launch of each step (one resident launch of
-    # SWEEPS sweeps), timed with CUDA events on its stream
+    # dominant kernel: the sweep launches of each step, timed with CUDA
+    # events on their stream
     plan = chain.plan()
-    k_launches_per_run = 1 if plan["kernel"] == 2 else SWEEPS * info.passes
+    if plan["kernel"] == 2:
+        # the library splits a run into launches of at most spl sweeps and at
+        # most 60000 * halo / passes sweeps (16-bit exchange tags)
+        per = max(1, 60000 * plan["halo"] // info.passes)
+        if plan["sweeps_per_launch"]:
+            per = min(per, plan["sweeps_per_launch"])
+        k_launches_per_run = -(-SWEEPS // per)
+    else:
+        k_launches_per_run = SWEEPS * info.passes
     k_ms = run_ms / run_launches / k_launches_per_run
     bytes_per_sweep = 2 * info.edges / 8
     alg_bytes_launch = bytes_per_sweep * SWEEPS / k_launches_per_run
     peak, peak_kind = peaks()
     achieved = alg_bytes_launch / (k_ms / 1e3) / 1e9
-    traffic = recorded_traffic(WORKLOAD) if plan["kernel"] == 2 else None
+    traffic = recorded_traffic(wl["name"]) if plan["kernel"] == 2 else None
 
     # end to end through the C-ABI with host buffers
     init_host = dom.initial_state()
-    h_out = np.empty((H, W), dtype=np.int32)
+    h_out = np.empty(hshape, dtype=np.int32)
     s_out = np.empty(dom.canon_shape, dtype=np.uint8)
-    n_out = np.empty((4, H - 1, W - 1), dtype=np.float64)
+    n_out = np.empty((4, info.height - 1, info.width - 1), dtype=np.float64) if density else None
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     barrier()
@@ -275,11 +350,13 @@ def run_ours(args):
     for _ in range(e2e_steps):
         chain.reset(stream=stream)
         chain.write_state(init_host, stream=stream)       # host -> device
-        chain.density_begin(STRIDE, BURN)
+        if density:
+            chain.density_begin(*density)
         chain.run(SWEEPS, stream=stream)
         chain.read_state(s_out, stream=stream)            # device -> host
         chain.read_height(h_out, stream=stream)
-        chain.read_nsew(n_out, stream=stream)
+        if density:
+            chain.read_nsew(n_out, stream=stream)
     torch.cuda.synchronize()
     chain.sync(stream)
     e2e_s = time.perf_counter() - t0
@@ -289,21 +366,23 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        r, dt = oracle_rate(BASELINE_SAMPLE_SWEEPS)
+        k = wl["baseline_sweeps"]
+        r, dt, _ = oracle_rate(wl, k, info.sites)
         cpu = {"value": r, "unit": "attempts/s", "cores": 1, "kind": "oracle",
-               "sample": "%d sweeps of the %s workload from the all-horizontal start (%.1f s)"
-                         % (BASELINE_SAMPLE_SWEEPS, WORKLOAD, dt)}
+               "sample": "%d sweeps of the %s workload from its start state (%.1f s)" % (k, wl["name"], dt)}
 
     if rank == 0:
+        cfg = {"workload": wl["name"], "size": list(wl["size"]), "sites": info.sites,
+               "sweeps_per_step": SWEEPS, "threshold": thr_desc, "seed": wl["seed"],
+               "l2": "flushed between steps (256 MB write); state is L2-sized",
+               "parallelism": "replicas" if world > 1 else "single"}
+        if density:
+            cfg.update(density_stride=density[0], burn_in=density[1])
+        d2h = int(s_out.nbytes + h_out.nbytes + (n_out.nbytes if density else 0))
         line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": N_ORDER, "sites": info.sites,
-                           "sweeps_per_step": SWEEPS, "density_stride": STRIDE, "burn_in": BURN,
-                           "threshold": UNIFORM_T, "seed": SEED,
-                           "l2": "flushed between steps (256 MB write); state is L2-sized",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                              "traffic": traffic, "kernel": "resident_kernel" if plan["kernel"] == 2
@@ -314,8 +393,7 @@ def run_ours(args):
                 "clocks": clocks,
                 "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "attempts/s",
-                        "h2d_bytes_per_step": int(init_host.nbytes),
-                        "d2h_bytes_per_step": int(s_out.nbytes + h_out.nbytes + n_out.nbytes)},
+                        "h2d_bytes_per_step": int(init_host.nbytes), "d2h_bytes_per_step": d2h},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -463,7 +541,7 @@ def main():
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["aztec2048", "batch", "serve"], default="aztec2048")
+    ap.add_argument("--workload", choices=[*WORKLOADS, "batch", "serve"], default="aztec2048")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=80.0)
@@ -478,6 +556,9 @@ def main():
         run_serve(args)
         return
     if args.impl == "reference":
+        if args.workload not in WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-chain workloads"}))
+            return
         run_reference(args)
     else:
         run_ours(args)

@@ -307,7 +307,7 @@ int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream);
  *  halo:              passes between boundary exchanges of the resident
  *                     kernel (1..64).
  *  threads:           threads per CTA of the resident kernel (512 or 1024).
- *  npre:              random bit planes generated ahead per group (1..8).
+ *  npre:              random bit planes generated ahead per group (1..16).
  * tl_chain_get_plan also fills the resolved values and ctas / smem_bytes. */
 typedef struct {
     int kernel;

@@ -113,6 +113,14 @@ struct RndPre {
 // Same draw with the first `npre` planes read from shared memory: two loops,
 // so the on-the-spot Philox of later planes is never evaluated for the
 // planes that were generated ahead.
+TL_DEV void hb_compare(uint4& lt, uint4& und, uint4 o, uint4 t)
+{
+    uint32_t d;
+    d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
+    d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
+    d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
+    d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+}
 template <class TB>
 TL_DEV uint4 heat_bath(uint4 f, int kmax, const RndPre& rnd, const TB& tb)
 {
@@ -122,23 +130,11 @@ TL_DEV uint4 heat_bath(uint4 f, int kmax, const RndPre& rnd, const TB& tb)
     int k = 0;
     for (; k < kp; ++k) {
         if (!any4(und)) return lt;
-        const uint4 o = rnd.pre[(size_t)k * rnd.stride];
-        const uint4 t = tb(k);
-        uint32_t d;
-        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
-        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
-        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
-        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+        hb_compare(lt, und, rnd.pre[(size_t)k * rnd.stride], tb(k));
     }
     for (; k <= kmax; ++k) {
         if (!any4(und)) break;
-        const uint4 o = rnd.more(k);
-        const uint4 t = tb(k);
-        uint32_t d;
-        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
-        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
-        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
-        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+        hb_compare(lt, und, rnd.more(k), tb(k));
     }
     return lt;
 }
@@ -182,11 +178,14 @@ TL_DEV uint32_t lut16(uint32_t tl, uint32_t tr, uint32_t br, uint32_t bl, uint32
 // of t16[idx] is set, else zero (16 words per plane), so each level of the
 // selection tree is one three-input bitwise select.
 TL_DEV uint32_t sel(uint32_t c, uint32_t a1, uint32_t a0) { return (c & a1) | (~c & a0); }
+// T must be 16-byte aligned (four vector loads).
 TL_DEV uint32_t lut16_tab(uint32_t tl, uint32_t tr, uint32_t br, uint32_t bl, const uint32_t* T)
 {
-    const uint32_t v0 = sel(tl, T[1], T[0]), v1 = sel(tl, T[3], T[2]), v2 = sel(tl, T[5], T[4]),
-                   v3 = sel(tl, T[7], T[6]), v4 = sel(tl, T[9], T[8]), v5 = sel(tl, T[11], T[10]),
-                   v6 = sel(tl, T[13], T[12]), v7 = sel(tl, T[15], T[14]);
+    const uint4* T4 = reinterpret_cast<const uint4*>(T);
+    const uint4 a = T4[0], b = T4[1], c = T4[2], d = T4[3];
+    const uint32_t v0 = sel(tl, a.y, a.x), v1 = sel(tl, a.w, a.z), v2 = sel(tl, b.y, b.x),
+                   v3 = sel(tl, b.w, b.z), v4 = sel(tl, c.y, c.x), v5 = sel(tl, c.w, c.z),
+                   v6 = sel(tl, d.y, d.x), v7 = sel(tl, d.w, d.z);
     const uint32_t w0 = sel(tr, v1, v0), w1 = sel(tr, v3, v2), w2 = sel(tr, v5, v4), w3 = sel(tr, v7, v6);
     return sel(bl, sel(br, w3, w2), sel(br, w1, w0));
 }
@@ -206,6 +205,38 @@ struct TbTable {
                           lut16(tl.z, tr.z, br.z, bl.z, tt), lut16(tl.w, tr.w, br.w, bl.w, tt));
     }
 };
+
+// Count form of the six-vertex lookup: x_i = corner bit i XOR polarity bit
+// i, n = x_0 + x_1 + x_2 + x_3 in bit-sliced binary (n0, n1, n2), and the
+// threshold bit of plane k is entry n of C_k = ctab + 8k (C_k[n] all ones
+// where bit 31-k of t5[n] is set).  C must be 16-byte aligned.
+TL_DEV void corner_count(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3, uint32_t& n0, uint32_t& n1,
+                         uint32_t& n2)
+{
+    const uint32_t a = x0 ^ x1, b = x0 & x1, c = x2 ^ x3, d = x2 & x3;
+    const uint32_t e = a & c;        // carry of the low bits (then b = d = 0)
+    n0 = a ^ c;
+    n1 = b ^ d ^ e;
+    n2 = b & d;                      // n = 4
+}
+TL_DEV uint32_t lut5(uint32_t n0, uint32_t n1, uint32_t n2, uint4 c03, uint32_t c4)
+{
+    return sel(n2, c4, sel(n1, sel(n0, c03.w, c03.z), sel(n0, c03.y, c03.x)));
+}
+struct TbCount {
+    const uint32_t* ctab;   // expanded [32][8], entries 0..4 used
+    uint4 n0, n1, n2;
+    TL_DEV uint4 operator()(int k) const
+    {
+        const uint32_t* C = ctab + 8 * k;
+        const uint4 c03 = *reinterpret_cast<const uint4*>(C);
+        const uint32_t c4 = C[4];
+        return make_uint4(lut5(n0.x, n1.x, n2.x, c03, c4), lut5(n0.y, n1.y, n2.y, c03, c4),
+                          lut5(n0.z, n1.z, n2.z, c03, c4), lut5(n0.w, n1.w, n2.w, c03, c4));
+    }
+};
+// All-ones where polarity bit i of `pol` is set.
+TL_DEV uint32_t polmask(int pol, int i) { return ((pol >> i) & 1) ? 0xFFFFFFFFu : 0u; }
 
 TL_DEV uint32_t range_mask(int k, int jlo, int jhi)
 {
@@ -410,7 +441,7 @@ TL_DEV int sixv_py(uint32_t pass) { return (pass == 1u || pass == 3u) ? 1 : 0; }
 
 template <class RND>
 TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, uint32_t pass,
-                        const RND& rnd, const ThrView& th, const uint32_t* ttab)
+                        const RND& rnd, const ThrView& th, const uint32_t* ttab, const uint32_t* ctab)
 {
     const int px = sixv_px(pass);
     const int k0 = m << 2;
@@ -448,8 +479,21 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
     f.x = TL_6V_F(x, 0); f.y = TL_6V_F(y, 1); f.z = TL_6V_F(z, 2); f.w = TL_6V_F(w, 3);
 #undef TL_6V_F
     if (!any4(f)) return;
-    TbTable tb{th.tmask, ttab, TL, TR, BR, BL};
-    const uint4 lt = heat_bath(f, 31, rnd, tb);
+    uint4 lt;
+    if (ctab) {
+        const uint32_t p0 = polmask(th.cpol, 0), p1 = polmask(th.cpol, 1), p2 = polmask(th.cpol, 2),
+                       p3 = polmask(th.cpol, 3);
+        TbCount tb;
+        tb.ctab = ctab;
+        corner_count(TL.x ^ p0, TR.x ^ p1, BR.x ^ p2, BL.x ^ p3, tb.n0.x, tb.n1.x, tb.n2.x);
+        corner_count(TL.y ^ p0, TR.y ^ p1, BR.y ^ p2, BL.y ^ p3, tb.n0.y, tb.n1.y, tb.n2.y);
+        corner_count(TL.z ^ p0, TR.z ^ p1, BR.z ^ p2, BL.z ^ p3, tb.n0.z, tb.n1.z, tb.n2.z);
+        corner_count(TL.w ^ p0, TR.w ^ p1, BR.w ^ p2, BL.w ^ p3, tb.n0.w, tb.n1.w, tb.n2.w);
+        lt = heat_bath(f, 31, rnd, tb);
+    } else {
+        TbTable tb{th.tmask, ttab, TL, TR, BR, BL};
+        lt = heat_bath(f, 31, rnd, tb);
+    }
     const uint4 fl = make_uint4(f.x & (lt.x ^ B.x), f.y & (lt.y ^ B.y), f.z & (lt.z ^ B.z),
                                 f.w & (lt.w ^ B.w));
     if (!any4(fl)) return;
@@ -462,14 +506,16 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
 
 
 // Dispatch one group update for lattice LAT.
-// `ttab`: expanded six-vertex table in shared memory, or nullptr.
+// `ttab`: expanded six-vertex table in shared memory, or nullptr; `ctab`:
+// expanded count table (used instead when not nullptr).
 template <int LAT, int TK, class RND>
 TL_DEV void group_update(uint32_t* row, int64_t RW, const Geom& g, int y, int m, uint32_t pass,
-                         const RND& rnd, const ThrView& th, const uint32_t* ttab = nullptr)
+                         const RND& rnd, const ThrView& th, const uint32_t* ttab = nullptr,
+                         const uint32_t* ctab = nullptr)
 {
     if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
     else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
-    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th, ttab);
+    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th, ttab, ctab);
 }
 
 // splitmix64 output for state x (Steele, Lea & Flood 2014).

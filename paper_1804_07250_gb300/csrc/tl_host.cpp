@@ -725,6 +725,30 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
             for (int idx = 0; idx < 16; ++idx) m |= ((th->table16[idx] >> (31 - k)) & 1u) << idx;
             c->th.tmask[k] = m;
         }
+        // tables that depend only on how many corner bits differ from a fixed
+        // polarity (the symmetric weights a1 = a2 = b1 = b2, c1 = c2 among
+        // them) take a cheaper lookup: a bit-sliced corner count and a
+        // 5-entry table
+        c->th.cpol = -1;
+        for (int pol = 0; pol < 16 && c->th.cpol < 0; ++pol) {
+            uint32_t t5[5];
+            bool seen[5] = {false, false, false, false, false}, ok = true;
+            for (int idx = 0; idx < 16 && ok; ++idx) {
+                const int n = __builtin_popcount((unsigned)(idx ^ pol));
+                if (!seen[n]) {
+                    seen[n] = true;
+                    t5[n] = th->table16[idx];
+                } else if (t5[n] != th->table16[idx]) {
+                    ok = false;
+                }
+            }
+            if (ok) {
+                c->th.cpol = pol;
+                for (int n = 0; n < 5; ++n) c->th.t5[n] = t5[n];
+            }
+        }
+    } else {
+        c->th.cpol = -1;
     }
     if (th->kind == TL_T_SITE) {
         const size_t nplanes = (size_t)g.H * g.npar * 32 * g.K;
@@ -787,7 +811,7 @@ TL_API int tl_chain_set_plan(tl_chain* c, const tl_plan* p)
 {
     if (!c || !p || p->kernel < 0 || p->kernel > 2 || p->sweeps_per_launch < 0 || p->halo < 0 ||
         p->halo > 64 || (p->threads != 0 && p->threads != 512 && p->threads != 1024) || p->npre < 0 ||
-        p->npre > 8)
+        p->npre > 16)
         return fail(TL_EINVAL, "tl_chain_set_plan: bad plan");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     c->kernel = p->kernel;

@@ -49,6 +49,8 @@ struct ThrView {
     int kmax;               // last plane that can decide a scalar compare
     const uint32_t* planes; // THR_SITE: [H][npar][32][K] threshold bit planes
     uint32_t tmask[32];     // THR_TABLE: bit idx of tmask[k] = bit 31-k of t16[idx]
+    int cpol;               // THR_TABLE: -1, or a 4-bit polarity p with t16[idx] = t5[popc(idx ^ p)]
+    uint32_t t5[5];
 };
 
 // Height propagation plan (per height-grid row): domain interval

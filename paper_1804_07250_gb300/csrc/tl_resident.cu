@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     __shared__ int4 s_ptab[64];
     __shared__ uint32_t s_psweep[64];
     __shared__ uint32_t s_next_sweep, s_next_pass;
-    __shared__ uint32_t s_ttab[LAT == LAT_SIXV ? 32 * 16 : 1];   // expanded six-vertex table
+    __shared__ __align__(16) uint32_t s_ttab[LAT == LAT_SIXV ? 32 * 16 : 4];   // expanded six-vertex table
+    __shared__ __align__(16) uint32_t s_ctab[LAT == LAT_SIXV ? 32 * 8 : 4];    // expanded count table
     const Geom& g = P.g;
     const int64_t RW = g.row_words;
     const int c = blockIdx.x, C = gridDim.x;
@@ -164,8 +165,14 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     uint2* fitems = reinterpret_cast<uint2*>((reinterpret_cast<uintptr_t>(off + NTAB * (nloc + 1)) + 7) & ~(uintptr_t)7);
 
     copy_rows_from_global(sm, P.rows0 + (int64_t)slo * RW, (int64_t)nloc * RW, tid, NT);
-    if (LAT == LAT_SIXV)
+    if (LAT == LAT_SIXV) {
         for (int i = tid; i < 32 * 16; i += NT) s_ttab[i] = ((P.th.tmask[i >> 4] >> (i & 15)) & 1u) ? 0xFFFFFFFFu : 0u;
+        for (int i = tid; i < 32 * 8; i += NT) {
+            const int n = i & 7;
+            s_ctab[i] = (n < 5 && ((P.th.t5[n] >> (31 - (i >> 3))) & 1u)) ? 0xFFFFFFFFu : 0u;
+        }
+    }
+    const uint32_t* ctab = (LAT == LAT_SIXV && P.th.cpol >= 0) ? s_ctab : nullptr;
 
     // item tables: active groups of each local row (six-vertex: one table per
     // face-row parity), prefix offsets per table
@@ -240,25 +247,37 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             s_next_pass = pass;
         }
         __syncthreads();
-        // random planes of one pass (generator warps)
+        // random planes of one pass (generator warps): one thread per
+        // (plane, group) pair, pairs numbered plane-major so that neighbouring
+        // threads write neighbouring 16-byte slots; two Philox calls in flight
+        // per thread.  k = idx / e.y by a multiply-high with ceil(2^32 / e.y)
+        // (too large by at most one, then corrected; e.y = 1 needs none).
         auto gen = [&](int i) {
             const int4 e = s_ptab[i];
+            if (e.y <= 0) return;
             const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
-            for (int it = rtid; it < e.y; it += HALF) {
-                const uint32_t item = items[e.x + it];
-                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
-                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                // four planes at a time: independent chains the scheduler interleaves
-                for (int k0 = 0; k0 < P.npre; k0 += 4) {
-                    uint4 o[4];
+            const uint32_t d = (uint32_t)e.y, mg = 0xFFFFFFFFu / d + 1u;
+            const int n = P.npre * e.y;
+            for (int b0 = rtid; b0 < n; b0 += 2 * HALF) {
+                uint4 o[2];
+                int slot[2];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        o[q] = philox10(grp, sweep, ((uint32_t)(k0 + q) << 16) | pass, P.rng.stream, P.rng.k0,
-                                        P.rng.k1);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (k0 + q < P.npre) rbuf[(size_t)(k0 + q) * cap + e.z + it] = o[q];
+                for (int q = 0; q < 2; ++q) {
+                    const int idx = b0 + q * HALF;
+                    slot[q] = -1;
+                    if (idx >= n) continue;
+                    uint32_t k = d == 1u ? (uint32_t)idx : __umulhi((uint32_t)idx, mg);
+                    if (k * d > (uint32_t)idx) --k;
+                    const int it = idx - (int)(k * d);
+                    const uint32_t item = items[e.x + it];
+                    const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+                    const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+                    o[q] = philox10(grp, sweep, (k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
+                    slot[q] = (int)k * cap + e.z + it;
                 }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (slot[q] >= 0) rbuf[slot[q]] = o[q];
             }
         };
         if (!upd_role) gen(0);
@@ -295,7 +314,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
                     const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
                     group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th,
-                                          LAT == LAT_SIXV ? s_ttab : nullptr);
+                                          LAT == LAT_SIXV ? s_ttab : nullptr, ctab);
                 }
             } else if (i + 1 < hc) {
                 gen(i + 1);

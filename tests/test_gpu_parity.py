@@ -160,6 +160,30 @@ def test_resident_kernel_threads_npre(T, ctx, kind, args, threads, npre):
     _run_pair(T, ctx, kind, args, seed=29, k=20, kernel=2, threads=threads, npre=npre, **kw)
 
 
+@pytest.mark.parametrize("npre", [1, 8, 16])
+@pytest.mark.parametrize("case", ["aztec_t", "aztec_site", "hex", "hex_site", "dwbc", "dwbc_w", "dwbc_flat"])
+def test_resident_threshold_kinds(T, ctx, case, npre):
+    # every threshold form through the resident kernel: scalar and per-site
+    # (random 32-bit values), and six-vertex tables in count form (c = sqrt 2,
+    # all weights equal) and general form (random weights)
+    rng = np.random.default_rng([41, npre])
+    if case.startswith("aztec"):
+        kind, args = "aztec", (110,)
+    elif case.startswith("hex"):
+        kind, args = "hex", (70, 55, 64)
+    else:
+        kind, args = "dwbc", (170,)
+    if case.endswith("_site"):
+        shape = _oracle_state(kind, args).shape[1:]
+        kw = dict(site=rng.integers(0, 1 << 32, size=shape, dtype=np.uint64).astype(np.uint32))
+    elif kind == "dwbc":
+        kw = dict(w6={"dwbc": SQ2, "dwbc_flat": [1.0] * 6,
+                      "dwbc_w": list(np.exp(0.7 * rng.standard_normal(6)))}[case])
+    else:
+        kw = dict(scalar=0x7FF80000 if kind == "hex" else 0x9E3779B9)
+    _run_pair(T, ctx, kind, args, seed=43, stream=5, k=24, kernel=2, npre=npre, **kw)
+
+
 @pytest.mark.parametrize("spl", [1, 4, 7])
 def test_resident_kernel_launch_splits(T, ctx, spl):
     _run_pair(T, ctx, "aztec", (128,), seed=31, k=30, kernel=2, spl=spl, scalar=1 << 31)
