@@ -149,6 +149,38 @@ int tl_domain_get_info(const tl_domain* d, tl_domain_info* out);
  * canon_bytes). */
 int tl_domain_initial_state(const tl_domain* d, uint8_t* canon, size_t cap);
 
+/* Extreme configurations (Sec. 1.1: the maximal and minimal tilings T_max
+ * and T_min of the distributive lattice of tilings, found by Thurston's
+ * algorithm in time proportional to the domain size).  TL_EXTREME_TOP has
+ * the largest height function (dominoes: Fig. 2 with h = 0 at the first
+ * domain vertex; lozenges: every rotatable site UP, a full box for a
+ * hexagon; six-vertex: every face in state B, the anti-diagonal permutation
+ * for the domain wall), TL_EXTREME_BOTTOM the smallest (lozenges and
+ * six-vertex: every rotatable site DOWN, the built-in starting
+ * configurations).  For dominoes a rotation raises the height at sites of
+ * one colour and lowers it at the other, so both mix UP and DOWN blocks;
+ * the all-horizontal start of the Aztec diamond of order n is T_max for
+ * even n and T_min for odd n.  These are the two chains started by coupling
+ * from the past (Sec. 1.1.4).  `canon` is host memory, cap >= canon_bytes.
+ * Errors: TL_EINVAL. */
+#define TL_EXTREME_BOTTOM 0
+#define TL_EXTREME_TOP 1
+int tl_domain_extreme_state(const tl_domain* d, int which, uint8_t* canon, size_t cap);
+
+/* Domain enclosed by a closed lattice path (Sec. 1.1: a simply-connected
+ * union of faces; tileability and a starting tiling by Thurston's
+ * algorithm).  The path starts at a lattice point and takes `nsteps` unit
+ * steps `steps[i]`:
+ *   TL_DOMINO: 0 = +x, 1 = +y, 2 = -x, 3 = -y (square lattice);
+ *   TL_LOZENGE: 0 = +x, 1 = +y, 2 = +x+y, 3 = -x, 4 = -y, 5 = -x-y
+ *   (triangular lattice in the axial coordinates of the canonical layout).
+ * It must return to its start and visit no other point twice; either
+ * orientation.  The domain is translated so that the path's lowest x and y
+ * are 0; its starting configuration is TL_EXTREME_BOTTOM.  Errors:
+ * TL_EINVAL (bad lattice or step, path not closed, too large),
+ * TL_ENOTSIMPLY (path crosses itself), TL_ENOTTILEABLE (no tiling). */
+int tl_domain_from_boundary(int lattice, const int8_t* steps, size_t nsteps, tl_domain** out);
+
 /* ------------------------------------------------------------------------
  * Heat-bath thresholds, computed once on the host in FP64.  In each case
  * t = floor(P(UP) * 2^32), clamped to [0, 2^32 - 1], with P(UP) evaluated
@@ -227,6 +259,28 @@ int tl_chain_reset(tl_chain* c, void* stream);
 
 /* Absolute sweep index of the chain (number of sweeps run so far). */
 uint64_t tl_chain_sweep(const tl_chain* c);
+
+/* Set the absolute index of the next sweep (0 .. 2^32 - 1).  Random numbers
+ * are keyed by this index, so seeking replays or skips randomness; coupling
+ * from the past uses it to place runs at negative times.  Sweeps run after a
+ * seek must stay below 2^32.  Errors: TL_EINVAL. */
+int tl_chain_seek(tl_chain* c, uint64_t sweep);
+
+/* Exact sample by coupling from the past (Sec. 1.1.4; Propp and Wilson).
+ * Two chains start from TL_EXTREME_TOP and TL_EXTREME_BOTTOM with the same
+ * seed and stream id and run the sweeps with absolute indices 2^32 - T ..
+ * 2^32 - 1 (negative times -T .. -1), for T = t0, 2 t0, 4 t0, ...; the
+ * heat-bath move is monotone for dominoes and lozenges (and for the
+ * six-vertex model when a <= c and b <= c, Sec. 1.2.4), so once both chains
+ * end in the same configuration every start would have, and that
+ * configuration is an exact sample.  Coalescence is detected by equal state
+ * hashes and confirmed by comparing the configurations.  The result goes to
+ * `canon_out` (host or device, cap >= canon_bytes) and the T used to
+ * *t_used.  Synchronous.  Errors: TL_EINVAL (t0 < 1, tmax < t0 or tmax >
+ * 2^31), TL_EBUDGET (no coalescence within tmax sweeps), TL_ENOMEM,
+ * TL_ECUDA, TL_ETIMEOUT. */
+int tl_cftp(tl_ctx* ctx, const tl_domain* d, uint64_t seed, uint32_t stream_id, const tl_thresholds* th,
+            uint64_t t0, uint64_t tmax, uint8_t* canon_out, size_t cap, uint64_t* t_used, void* stream);
 
 /* Run k sweeps (the loop of RandomWalk, Sec. 2.2, with a fixed pass order)
  * on `stream`.  Enqueues only.  Density samples due inside the range (see

@@ -312,3 +312,215 @@ def accumulate(st: np.ndarray, counts: np.ndarray) -> None:
     """Edge-occupancy counters: counts += st (uint32, same shape)."""
     assert counts.dtype == np.uint32 and counts.shape == st.shape
     lib().or_accumulate(_p(st), st.size, _p(counts))
+
+
+# --------------------------------------------------------------------------
+# Regions from a boundary path, extreme tilings, coupling from the past
+# --------------------------------------------------------------------------
+_STEPS = {DOMINO: [(1, 0), (0, 1), (-1, 0), (0, -1)],
+          LOZENGE: [(1, 0), (0, 1), (1, 1), (-1, 0), (0, -1), (-1, -1)]}
+
+
+def _crossings(poly, W, H, offsets):
+    """Winding numbers of points (x + ox, y + oy) for every lattice (x, y) and
+    offset (ox, oy): the signed number of polygon edges crossing the ray from
+    the point towards +x (each edge spans one row band, the path having unit
+    steps).  Returns one [H, W] int array per offset."""
+    out = []
+    for ox, oy in offsets:
+        cnt = np.zeros((H, W + 1), dtype=np.int64)
+        n = len(poly)
+        for i in range(n):
+            (x0, y0), (x1, y1) = poly[i], poly[(i + 1) % n]
+            if y0 == y1:
+                continue
+            yb = min(y0, y1)                  # band [yb, yb + 1]
+            py = yb + oy
+            xc = x0 + (py - y0) * (x1 - x0) / (y1 - y0)
+            # points with x + ox < xc see the crossing
+            k = int(np.ceil(xc - ox))         # x < k
+            k = min(max(k, 0), W)
+            cnt[yb, 0] += 1 if y1 > y0 else -1
+            cnt[yb, k] -= 1 if y1 > y0 else -1
+        out.append(np.cumsum(cnt, axis=1)[:, :W])
+    return out
+
+
+def region_from_boundary(lattice: str, steps):
+    """Cells enclosed by a closed lattice path (Sec. 1.1: a domain is a union
+    of faces), by the winding number of the path around each cell centre.
+
+    Domino: returns (face [H-1, W-1] bool, W, H).  Lozenge: returns
+    (up [H, W], dn [H, W], W, H); up(x,y) has corners (x,y), (x+1,y),
+    (x+1,y+1) and dn(x,y) has (x,y), (x+1,y+1), (x,y+1).  The path is shifted
+    so that its smallest coordinates are 0.
+    """
+    pts = [(0, 0)]
+    for s in steps:
+        dx, dy = _STEPS[lattice][s]
+        pts.append((pts[-1][0] + dx, pts[-1][1] + dy))
+    assert pts[-1] == (0, 0), "path not closed"
+    assert len(set(pts[:-1])) == len(pts) - 1, "path not simple"
+    x0, y0 = min(p[0] for p in pts), min(p[1] for p in pts)
+    poly = [(x - x0, y - y0) for x, y in pts[:-1]]
+    W = max(p[0] for p in poly) + 1
+    H = max(p[1] for p in poly) + 1
+    if lattice == DOMINO:
+        (w,) = _crossings(poly, W, H, [(0.5, 0.5)])
+        return (w[:H - 1, :W - 1] != 0), W, H
+    wu, wd = _crossings(poly, W, H, [(2 / 3, 1 / 3), (1 / 3, 2 / 3)])
+    up, dn = wu != 0, wd != 0
+    up[H - 1, :] = False
+    up[:, W - 1] = False
+    dn[H - 1, :] = False
+    dn[:, W - 1] = False
+    return up, dn, W, H
+
+
+def tiling_by_search(lattice: str, region):
+    """Some tiling of a region by depth-first search (first uncovered cell
+    in (y, x) order, every way of covering it); None if there is none."""
+    if lattice == DOMINO:
+        face, W, H = region
+        cells = [(y, x) for y in range(H - 1) for x in range(W - 1) if face[y, x]]
+        inside = set(cells)
+
+        def partners(c):
+            y, x = c
+            return [(y, x + 1), (y + 1, x), (y, x - 1), (y - 1, x)]
+    else:
+        up, dn, W, H = region
+        cells = [(y, x, t) for y in range(H) for x in range(W) for t in (0, 1)
+                 if (up if t == 0 else dn)[y, x]]
+        inside = set(cells)
+
+        def partners(c):
+            y, x, t = c
+            # up(x,y) meets dn(x,y-1) across E1(x,y), dn(x,y) across E3(x,y)
+            # and dn(x+1,y) across E2(x+1,y)
+            if t == 0:
+                return [(y - 1, x, 1), (y, x, 1), (y, x + 1, 1)]
+            return [(y + 1, x, 0), (y, x, 0), (y, x - 1, 0)]
+    order = sorted(cells)
+    nbr = {c: [q for q in partners(c) if q in inside] for c in cells}
+    free = {c: len(nbr[c]) for c in cells}      # uncovered partners of each cell
+    covered = set()
+    pairs = []
+
+    def place(c, q, cand):
+        covered.update((c, q))
+        pairs.append((c, q))
+        for r in nbr[c] + nbr[q]:
+            if r not in covered:
+                free[r] -= 1
+                if free[r] <= 1:
+                    cand.append(r)
+
+    def unplace():
+        c, q = pairs[-1]
+        for r in nbr[c] + nbr[q]:
+            if r not in covered:
+                free[r] += 1
+        pairs.pop()
+        covered.difference_update((c, q))
+
+    def propagate(cand):
+        # cover every cell that has a single uncovered partner left; False on
+        # a cell with none.  Returns (ok, number of dominoes placed).
+        n = 0
+        while cand:
+            r = cand.pop()
+            if r in covered:
+                continue
+            if free[r] == 0:
+                return False, n
+            if free[r] == 1:
+                q = next(q for q in nbr[r] if q not in covered)
+                place(r, q, cand)
+                n += 1
+        return True, n
+
+    def solve(i):
+        # the first uncovered cell is at or after position i
+        while i < len(order) and order[i] in covered:
+            i += 1
+        if i == len(order):
+            return True
+        c = order[i]
+        for q in nbr[c]:
+            if q in covered:
+                continue
+            cand = []
+            place(c, q, cand)
+            ok, n = propagate(cand)
+            if ok and solve(i + 1):
+                return True
+            for _ in range(n + 1):
+                unplace()
+        return False
+
+    import sys
+    sys.setrecursionlimit(max(10000, 4 * len(cells)))
+    cand = [c for c in cells if free[c] <= 1]
+    ok, _ = propagate(cand)
+    if not ok or not solve(0):
+        return None
+    if lattice == DOMINO:
+        st = np.zeros((2, H, W), dtype=np.uint8)
+        for (y, x), (y2, x2) in pairs:
+            if y2 == y:      # horizontal domino crosses the vertical edge between its squares
+                st[1, y, max(x, x2)] = 1
+            else:            # vertical domino crosses the horizontal edge between its squares
+                st[0, max(y, y2), x] = 1
+        return st
+    st = np.zeros((3, H, W), dtype=np.uint8)
+    for a, b in pairs:
+        (y, x, t), (y2, x2, t2) = (a, b) if a[2] == 0 else (b, a)   # (up, down)
+        if y2 == y - 1:
+            st[0, y, x] = 1          # E1(x,y)
+        elif x2 == x:
+            st[2, y, x] = 1          # E3(x,y)
+        else:
+            st[1, y, x + 1] = 1      # E2(x+1,y)
+    return st
+
+
+def extreme(lattice: str, st: np.ndarray, top: bool) -> np.ndarray:
+    """T_max (top) or T_min of the region tiled by `st` (Sec. 1.1): apply
+    whole-class rotations while they move the height function pointwise up
+    (down) until none does.  A class move with all decisions equal moves
+    every rotated site of the class the same way."""
+    st = st.copy()
+    h, bad = height(lattice, st)
+    assert bad == 0
+    while True:
+        moved = False
+        for p in range(PASSES[lattice]):
+            for up in (1, 0):
+                trial = st.copy()
+                apply_pass(lattice, trial, p, np.full(st.shape[1:], up, np.uint8))
+                if np.array_equal(trial, st):
+                    continue
+                h2, _ = height(lattice, trial)
+                better = np.all(h2 >= h) if top else np.all(h2 <= h)
+                if better:
+                    st, h, moved = trial, h2, True
+        if not moved:
+            return st
+
+
+def cftp(lattice: str, st_top: np.ndarray, st_bot: np.ndarray, *, seed: int, stream: int = 0,
+         t0: int = 64, tmax: int = 1 << 31, **thr):
+    """Coupling from the past (Sec. 1.1.4): chains from T_max and T_min run the
+    sweeps of negative times -T..-1 (absolute sweep indices 2^32 - T ..
+    2^32 - 1), T doubling until they agree; returns (sample, T)."""
+    T = t0
+    while True:
+        a, b = st_top.copy(), st_bot.copy()
+        sweeps(lattice, a, seed=seed, stream=stream, sweep0=(1 << 32) - T, k=T, **thr)
+        sweeps(lattice, b, seed=seed, stream=stream, sweep0=(1 << 32) - T, k=T, **thr)
+        if np.array_equal(a, b):
+            return a, T
+        if 2 * T > tmax:
+            raise RuntimeError("no coalescence within %d sweeps" % T)
+        T *= 2

@@ -86,6 +86,8 @@ _SIG = {
     "tl_domain_destroy": (None, [_vp]),
     "tl_domain_get_info": (_i, [_vp, ctypes.POINTER(DomainInfo)]),
     "tl_domain_initial_state": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "tl_domain_extreme_state": (_i, [_vp, _i, _vp, ctypes.c_size_t]),
+    "tl_domain_from_boundary": (_i, [_i, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "tl_thresholds_domino_edge_weights": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]),
     "tl_thresholds_lozenge_q": (_i, [ctypes.c_double, _vp, _vp]),
     "tl_thresholds_lognormal_device": (_i, [_vp, ctypes.c_double, _u64, _vp, ctypes.c_size_t, _vp]),
@@ -95,6 +97,9 @@ _SIG = {
     "tl_chain_destroy": (None, [_vp]),
     "tl_chain_reset": (_i, [_vp, _vp]),
     "tl_chain_sweep": (_u64, [_vp]),
+    "tl_chain_seek": (_i, [_vp, _u64]),
+    "tl_cftp": (_i, [_vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds), _u64, _u64, _vp, ctypes.c_size_t,
+                     ctypes.POINTER(_u64), _vp]),
     "tl_chain_launches": (_u64, [_vp]),
     "tl_chain_set_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
@@ -204,6 +209,15 @@ class Domain:
     def dwbc(cls, N):
         h = _vp(); _check(_lib.tl_domain_dwbc(N, ctypes.byref(h))); return cls(h)
 
+    @classmethod
+    def from_boundary(cls, lattice, steps):
+        """Domain enclosed by a closed lattice path: lattice DOMINO (steps 0..3 =
+        +x, +y, -x, -y) or LOZENGE (0..5 = +x, +y, +x+y, -x, -y, -x-y)."""
+        st = np.ascontiguousarray(steps, dtype=np.int8)
+        h = _vp()
+        _check(_lib.tl_domain_from_boundary(int(lattice), st.ctypes.data, st.size, ctypes.byref(h)))
+        return cls(h)
+
     @property
     def canon_shape(self):
         return (self.info.planes, self.info.height, self.info.width)
@@ -216,6 +230,13 @@ class Domain:
         out = np.zeros(self.canon_shape, dtype=np.uint8)
         p, n = _ptr(out)
         _check(_lib.tl_domain_initial_state(self._h, p, n))
+        return out
+
+    def extreme_state(self, which: str) -> np.ndarray:
+        """'top' (every rotatable site UP) or 'bottom' (every one DOWN)."""
+        out = np.zeros(self.canon_shape, dtype=np.uint8)
+        p, n = _ptr(out)
+        _check(_lib.tl_domain_extreme_state(self._h, {"bottom": 0, "top": 1}[which], p, n))
         return out
 
     def domino_thresholds(self, w: np.ndarray) -> np.ndarray:
@@ -278,6 +299,18 @@ def thresholds(scalar=None, site=None, table16=None) -> Thresholds:
     return th
 
 
+def cftp(ctx, domain, *, seed: int, stream_id: int = 0, th, t0: int = 64, tmax: int = 1 << 31,
+         out=None, stream=None):
+    """Exact sample by coupling from the past; returns (configuration, T)."""
+    if out is None:
+        out = np.zeros(domain.canon_shape, dtype=np.uint8)
+    p, n = _ptr(out)
+    t = _u64()
+    _check(_lib.tl_cftp(ctx._h, domain._h, seed, stream_id, ctypes.byref(th), t0, tmax, p, n, ctypes.byref(t),
+                        _stream(stream)))
+    return out, int(t.value)
+
+
 class Chain:
     """One Markov chain resident on the GPU."""
 
@@ -305,6 +338,9 @@ class Chain:
 
     def reset(self, stream=None):
         _check(_lib.tl_chain_reset(self._h, _stream(stream)))
+
+    def seek(self, sweep: int):
+        _check(_lib.tl_chain_seek(self._h, sweep))
 
     def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0,
                  threads: int = 0, npre: int = 0):

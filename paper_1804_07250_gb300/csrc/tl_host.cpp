@@ -2,6 +2,7 @@
 // heat-bath thresholds, chain state management and the launch planner.
 #include "tiling.h"
 #include "tl_internal.h"
+#include "tl_thurston.h"
 
 #include <cuda_runtime.h>
 
@@ -33,6 +34,12 @@ static int fail(int code, const char* fmt, ...)
     g_err = buf;
     return code;
 }
+
+#define TL_TRY(expr)                   \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != TL_OK) return rc_;  \
+    } while (0)
 
 #define CUDA_TRY(expr)                                                                  \
     do {                                                                                \
@@ -84,7 +91,8 @@ struct tl_domain {
     uint64_t sites = 0, edges = 0;
     std::vector<int2> grange;         // per site row: [first, last+1) active groups
     int hw = 0, hh = 0;
-    std::vector<int> hxlo, hxhi, hspine;
+    std::vector<int> hseg;            // height segments, 6 ints each (see plan_heights)
+    int nseg = 0;
     int kappa = 0;
 };
 
@@ -132,39 +140,80 @@ static void set_group_range(tl_domain* d, int row, int jmin, int jmax)
     else d->grange[row] = make_int2(std::max(0, (jmin >> 7) - 1), (jmax >> 7) + 1);
 }
 
-// Height rows over a grid of hw x hh points given a membership test for
-// points and for the horizontal / vertical unit steps between them.
+// Height segments over a grid of hw x hh points, given membership tests
+// for points, for the horizontal step (x,y)-(x+1,y) and for the vertical
+// step (x,y-1)-(x,y).  A segment is a maximal run of domain points of one
+// row joined by domain steps; segments are linked into a tree by vertical
+// steps, breadth first from the segment holding the first domain point in
+// (y, x) order, so every parent precedes its children.  Entry s of hseg is
+// (y, lo, hi, parent, xs, dir), dir = +1 if the segment lies above its
+// parent.  A domain whose segments are not all linked is not connected.
 template <class InV, class InH, class InVert>
 static int plan_heights(tl_domain* d, int hw, int hh, InV inv, InH inh, InVert invert)
 {
     d->hw = hw;
     d->hh = hh;
-    d->hxlo.assign(hh, 1);
-    d->hxhi.assign(hh, 0);
-    d->hspine.assign(hh, -1);
-    int prev = -1;
+    struct Seg {
+        int y, lo, hi;
+    };
+    std::vector<Seg> segs;
+    std::vector<int> row_first(hh + 1, 0);
     for (int y = 0; y < hh; ++y) {
-        int lo = -1, hi = -1;
-        for (int x = 0; x < hw; ++x)
-            if (inv(x, y)) {
-                if (lo < 0) lo = x;
-                hi = x;
+        row_first[y] = (int)segs.size();
+        int x = 0;
+        while (x < hw) {
+            if (!inv(x, y)) {
+                ++x;
+                continue;
             }
-        if (lo < 0) continue;
-        for (int x = lo; x < hi; ++x)
-            if (!inv(x, y) || !inh(x, y))
-                return fail(TL_EUNSUPPORTED, "height: row %d of the domain is not an interval", y);
-        d->hxlo[y] = lo;
-        d->hxhi[y] = hi;
-        if (prev >= 0) {
-            if (prev != y - 1) return fail(TL_EUNSUPPORTED, "height: domain rows are not contiguous");
-            int xs = -1;
-            for (int x = std::max(lo, d->hxlo[prev]); x <= std::min(hi, d->hxhi[prev]); ++x)
-                if (invert(x, y)) { xs = x; break; }
-            if (xs < 0) return fail(TL_EUNSUPPORTED, "height: rows %d and %d are not linked", y - 1, y);
-            d->hspine[y] = xs;
+            const int lo = x;
+            while (x + 1 < hw && inv(x + 1, y) && inh(x, y)) ++x;
+            segs.push_back(Seg{y, lo, x});
+            ++x;
         }
-        prev = y;
+    }
+    row_first[hh] = (int)segs.size();
+    const int n = (int)segs.size();
+    d->nseg = n;
+    d->hseg.assign((size_t)6 * n, 0);
+    if (n == 0) return TL_OK;
+    // breadth-first linking; `order` lists segments parent first
+    std::vector<int> parent(n, -2), xs(n, -1), dir(n, 0), order;
+    order.reserve(n);
+    parent[0] = -1;
+    order.push_back(0);
+    for (size_t qi = 0; qi < order.size(); ++qi) {
+        const Seg& sg = segs[order[qi]];
+        for (int dy = -1; dy <= 1; dy += 2) {
+            const int ny = sg.y + dy;
+            if (ny < 0 || ny >= hh) continue;
+            // unlinked segments of the neighbouring row that overlap this one
+            for (int t = row_first[ny]; t < row_first[ny + 1]; ++t) {
+                if (parent[t] != -2 || segs[t].hi < sg.lo || segs[t].lo > sg.hi) continue;
+                const int a = std::max(sg.lo, segs[t].lo), b = std::min(sg.hi, segs[t].hi);
+                for (int x = a; x <= b; ++x)
+                    if (invert(x, dy > 0 ? ny : sg.y)) {
+                        parent[t] = order[qi];
+                        xs[t] = x;
+                        dir[t] = dy;
+                        order.push_back(t);
+                        break;
+                    }
+            }
+        }
+    }
+    if ((int)order.size() != n) return fail(TL_ENOTSIMPLY, "height: the domain is not connected");
+    std::vector<int> pos(n);
+    for (int i = 0; i < n; ++i) pos[order[i]] = i;
+    for (int i = 0; i < n; ++i) {
+        const int sidx = order[i];
+        int* e = &d->hseg[(size_t)6 * i];
+        e[0] = segs[sidx].y;
+        e[1] = segs[sidx].lo;
+        e[2] = segs[sidx].hi;
+        e[3] = parent[sidx] < 0 ? -1 : pos[parent[sidx]];
+        e[4] = xs[sidx];
+        e[5] = dir[sidx];
     }
     return TL_OK;
 }
@@ -272,10 +321,17 @@ static int analyse_sixv(tl_domain* d)
     d->sites = (uint64_t)(N - 1) * (N - 1);
     d->edges = (uint64_t)2 * N * (N - 1);
     d->hw = d->hh = N + 1;
-    d->hxlo.assign(N + 1, 0);
-    d->hxhi.assign(N + 1, N);
-    d->hspine.assign(N + 1, 0);
-    d->hspine[0] = -1;
+    d->nseg = N + 1;
+    d->hseg.assign((size_t)6 * (N + 1), 0);
+    for (int y = 0; y <= N; ++y) {
+        int* e = &d->hseg[(size_t)6 * y];
+        e[0] = y;
+        e[1] = 0;
+        e[2] = N;
+        e[3] = y - 1;
+        e[4] = 0;
+        e[5] = 1;
+    }
     return TL_OK;
 }
 
@@ -382,6 +438,240 @@ TL_API int tl_domain_dwbc(int N, tl_domain** out)
         for (int Y = 0; Y < col; ++Y) vt[(size_t)Y * B + col] = 1;     // up column `col`
         for (int X = 0; X < col; ++X) hz[(size_t)col * B + X] = 1;     // left along row `col`
     }
+    return finish_domain(d, 0, out);
+}
+
+// ---------------------------------------------------------------------------
+// Extreme configurations and domains from a boundary path (Sec. 1.1: the
+// maximal and minimal tilings; tileability by Thurston's algorithm).
+// ---------------------------------------------------------------------------
+
+// Height edges of a domino region, faces given by F(x, y) (lower-left
+// corner (x, y)).  Along an edge the height rises by 1 if the face on its
+// left is black (x + y even) and falls by 1 otherwise; across a domino the
+// step is -3 times that (Fig. 2).
+template <class Face>
+static void domino_region(int W, int H, Face F, std::vector<uint8_t>& active, std::vector<HEdge>& edges)
+{
+    active.assign((size_t)W * H, 0);
+    edges.clear();
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            active[(size_t)y * W + x] = F(x, y) || F(x - 1, y) || F(x, y - 1) || F(x - 1, y - 1);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x + 1 < W; ++x) {
+            const bool a = F(x, y), b = F(x, y - 1);   // above, below (left, right of the step +x)
+            if (!a && !b) continue;
+            const int8_t af = ((x + y) & 1) == 0 ? 1 : -1;
+            edges.push_back(HEdge{y * W + x, y * W + x + 1, af, (int8_t)(-3 * af), (uint8_t)(a && b),
+                                  (int64_t)y * W + x});
+        }
+    for (int y = 0; y + 1 < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const bool l = F(x - 1, y), r = F(x, y);   // left, right of the step +y
+            if (!l && !r) continue;
+            const int8_t af = ((x - 1 + y) & 1) == 0 ? 1 : -1;
+            edges.push_back(HEdge{y * W + x, (y + 1) * W + x, af, (int8_t)(-3 * af), (uint8_t)(l && r),
+                                  (int64_t)H * W + (int64_t)y * W + x});
+        }
+}
+
+// Height edges of a lozenge region, triangles given by U(x, y) (vertices
+// (x,y), (x+1,y), (x+1,y+1)) and D(x, y) (vertices (x,y), (x+1,y+1),
+// (x,y+1)).  The height is the k-coordinate of the stepped surface: a free
+// E1 or E2 step keeps it and a crossed one (a lozenge's short diagonal)
+// lowers it by one; a free E3 step lowers it by one and a crossed one keeps it.
+template <class Up, class Dn>
+static void lozenge_region(int W, int H, Up U, Dn D, std::vector<uint8_t>& active, std::vector<HEdge>& edges)
+{
+    active.assign((size_t)W * H, 0);
+    edges.clear();
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            active[(size_t)y * W + x] =
+                U(x, y) || D(x, y) || U(x - 1, y) || D(x - 1, y - 1) || U(x - 1, y - 1) || D(x, y - 1);
+    const int64_t plane = (int64_t)W * H;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int v = y * W + x;
+            if (x + 1 < W) {   // E1: up(x,y) | down(x,y-1)
+                const bool a = U(x, y), b = D(x, y - 1);
+                if (a || b) edges.push_back(HEdge{v, v + 1, 0, -1, (uint8_t)(a && b), (int64_t)v});
+            }
+            if (y + 1 < H) {   // E2: down(x,y) | up(x-1,y)
+                const bool a = D(x, y), b = U(x - 1, y);
+                if (a || b) edges.push_back(HEdge{v, v + W, 0, -1, (uint8_t)(a && b), plane + v});
+            }
+            if (x + 1 < W && y + 1 < H) {   // E3: up(x,y) | down(x,y)
+                const bool a = U(x, y), b = D(x, y);
+                if (a || b) edges.push_back(HEdge{v, v + W + 1, -1, 0, (uint8_t)(a && b), 2 * plane + v});
+            }
+        }
+}
+
+// Configuration with the maximal (`up`) or minimal height function.  For
+// lozenges and the six-vertex model these are the configurations with every
+// rotatable site UP (a cube added; paths through B and L) or DOWN; for
+// dominoes a rotation raises the height at sites of one colour and lowers
+// it at the other, so T_max and T_min mix both kinds of blocks.
+static int extreme_config(const tl_domain* d, bool up, std::vector<uint8_t>& out)
+{
+    const Geom& g = d->g;
+    const int W = g.W, H = g.H;
+    out.assign(d->init.size(), 0);
+    if (g.lattice == LAT_SIXV) {
+        if (!up) {
+            out = d->init;
+            return TL_OK;
+        }
+        // paths hug the top right: the path entering column X rises to row N+1-X
+        const int N = g.N, B = N + 2;
+        uint8_t* hz = out.data();
+        uint8_t* vt = out.data() + (size_t)B * B;
+        for (int Y = 1; Y <= N; ++Y)
+            for (int X = 0; X <= N - Y; ++X) hz[(size_t)Y * B + X] = 1;
+        for (int X = 1; X <= N; ++X)
+            for (int Y = 0; Y <= N - X; ++Y) vt[(size_t)Y * B + X] = 1;
+        return TL_OK;
+    }
+    std::vector<uint8_t> active;
+    std::vector<HEdge> edges;
+    bool top;
+    if (g.lattice == LAT_DOMINO) {
+        auto F = [&](int x, int y) {
+            return x >= 0 && y >= 0 && x < W - 1 && y < H - 1 && d->cover[(size_t)y * (W - 1) + x] != 0;
+        };
+        domino_region(W, H, F, active, edges);
+        top = up;
+    } else {
+        const int TW = W + 1, TH = H + 1;
+        auto U = [&](int x, int y) {
+            return x >= -1 && y >= -1 && x < W && y < H && d->cover[(size_t)(y + 1) * TW + (x + 1)] != 0;
+        };
+        auto D = [&](int x, int y) {
+            return x >= -1 && y >= -1 && x < W && y < H &&
+                   d->cover[(size_t)TW * TH + (size_t)(y + 1) * TW + (x + 1)] != 0;
+        };
+        lozenge_region(W, H, U, D, active, edges);
+        top = up;
+    }
+    std::vector<int> h;
+    std::string why;
+    const int rc = thurston_heights(W * H, active, edges, top, h, why);
+    if (rc != TL_OK) return fail(rc, "extreme configuration: %s", why.c_str());
+    tiling_from_heights(edges, h, out.data());
+    return TL_OK;
+}
+
+TL_API int tl_domain_extreme_state(const tl_domain* d, int which, uint8_t* canon, size_t cap)
+{
+    if (!d || !canon || (which != TL_EXTREME_BOTTOM && which != TL_EXTREME_TOP))
+        return fail(TL_EINVAL, "tl_domain_extreme_state: bad argument");
+    if (cap < d->init.size()) return fail(TL_EINVAL, "tl_domain_extreme_state: cap %zu < %zu", cap, d->init.size());
+    std::vector<uint8_t> cfg;
+    TL_TRY(extreme_config(d, which == TL_EXTREME_TOP, cfg));
+    std::memcpy(canon, cfg.data(), cfg.size());
+    return TL_OK;
+}
+
+// Face (triangle) membership by winding number: for each cell the signed
+// count of path steps crossing a ray from its centre towards +x.
+TL_API int tl_domain_from_boundary(int lattice, const int8_t* steps, size_t nsteps, tl_domain** out)
+{
+    if (!out || !steps || (lattice != TL_DOMINO && lattice != TL_LOZENGE))
+        return fail(TL_EINVAL, "tl_domain_from_boundary: bad argument");
+    if (nsteps < 3 || nsteps > ((size_t)1 << 28)) return fail(TL_EINVAL, "tl_domain_from_boundary: %zu steps", nsteps);
+    static const int DX[2][6] = {{1, 0, -1, 0, 0, 0}, {1, 0, 1, -1, 0, -1}};
+    static const int DY[2][6] = {{0, 1, 0, -1, 0, 0}, {0, 1, 1, 0, -1, -1}};
+    const int L = lattice == TL_DOMINO ? 0 : 1, ndir = L ? 6 : 4;
+    std::vector<int64_t> px(nsteps + 1), py(nsteps + 1);
+    px[0] = py[0] = 0;
+    for (size_t i = 0; i < nsteps; ++i) {
+        const int s = steps[i];
+        if (s < 0 || s >= ndir) return fail(TL_EINVAL, "tl_domain_from_boundary: step %zu = %d", i, s);
+        px[i + 1] = px[i] + DX[L][s];
+        py[i + 1] = py[i] + DY[L][s];
+    }
+    if (px[nsteps] != 0 || py[nsteps] != 0) return fail(TL_EINVAL, "tl_domain_from_boundary: path is not closed");
+    const int64_t x0 = *std::min_element(px.begin(), px.end()), y0 = *std::min_element(py.begin(), py.end());
+    const int64_t W = *std::max_element(px.begin(), px.end()) - x0 + 1;
+    const int64_t H = *std::max_element(py.begin(), py.end()) - y0 + 1;
+    if (!box_ok(W, H)) return fail(TL_EINVAL, "tl_domain_from_boundary: box %lldx%lld", (long long)W, (long long)H);
+    {
+        std::vector<uint8_t> seen((size_t)W * H, 0);
+        for (size_t i = 0; i < nsteps; ++i) {
+            uint8_t& v = seen[(size_t)(py[i] - y0) * W + (px[i] - x0)];
+            if (v) return fail(TL_ENOTSIMPLY, "tl_domain_from_boundary: path visits a point twice (step %zu)", i);
+            v = 1;
+        }
+    }
+    // signed crossings per row band [y, y+1]: vertical (E2) steps at x, and
+    // for lozenges diagonal (E3) steps leaving row y at x
+    std::vector<int> cv((size_t)W * H, 0), cd((size_t)W * H, 0);
+    for (size_t i = 0; i < nsteps; ++i) {
+        const int64_t x = px[i] - x0, y = py[i] - y0;
+        const int s = steps[i], dx = DX[L][s], dy = DY[L][s];
+        if (dy == 0) continue;
+        const int64_t yb = dy > 0 ? y : y - 1;           // band crossed
+        const int64_t xb = dy > 0 ? x : x + dx;           // x of the step's lower end
+        int* arr = dx == 0 ? cv.data() : cd.data();
+        arr[(size_t)yb * W + xb] += dy;
+    }
+    // suffix sums: cells to the left of a crossing see it
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = W - 2; x >= 0; --x) {
+            cv[(size_t)y * W + x] += cv[(size_t)y * W + x + 1];
+            cd[(size_t)y * W + x] += cd[(size_t)y * W + x + 1];
+        }
+    auto SV = [&](int64_t x, int64_t y) { return x < W ? cv[(size_t)y * W + x] : 0; };
+    auto SD = [&](int64_t x, int64_t y) { return x < W ? cd[(size_t)y * W + x] : 0; };
+    tl_domain* d = new (std::nothrow) tl_domain();
+    if (!d) return fail(TL_ENOMEM, "tl_domain_from_boundary: host allocation");
+    std::vector<uint8_t> active;
+    std::vector<HEdge> edges;
+    int64_t cells = 0;
+    const bool top = false;   // start: T_min
+    if (!L) {
+        d->g = make_geom(LAT_DOMINO, (int)W, (int)H, 0);
+        std::vector<uint8_t> face((size_t)(W - 1) * (H - 1), 0);
+        for (int64_t y = 0; y + 1 < H; ++y)
+            for (int64_t x = 0; x + 1 < W; ++x) {
+                face[(size_t)y * (W - 1) + x] = SV(x + 1, y) != 0;   // centre (x + 1/2, y + 1/2)
+                cells += face[(size_t)y * (W - 1) + x];
+            }
+        auto F = [&](int x, int y) {
+            return x >= 0 && y >= 0 && x < W - 1 && y < H - 1 && face[(size_t)y * (W - 1) + x] != 0;
+        };
+        domino_region((int)W, (int)H, F, active, edges);
+    } else {
+        d->g = make_geom(LAT_LOZENGE, (int)W, (int)H, 0);
+        // up (x,y): centre (x + 2/3, y + 1/3); down (x,y): centre (x + 1/3, y + 2/3).
+        // A vertical step at x' crosses the ray iff x' >= x + 1; a diagonal
+        // step leaving row y at x' crosses at x' + 1/3 (up) or x' + 2/3 (down).
+        std::vector<uint8_t> up((size_t)W * H, 0), dn((size_t)W * H, 0);
+        for (int64_t y = 0; y + 1 < H; ++y)
+            for (int64_t x = 0; x + 1 < W; ++x) {
+                up[(size_t)y * W + x] = (SV(x + 1, y) + SD(x + 1, y)) != 0;
+                dn[(size_t)y * W + x] = (SV(x + 1, y) + SD(x, y)) != 0;
+                cells += up[(size_t)y * W + x] + dn[(size_t)y * W + x];
+            }
+        auto U = [&](int x, int y) { return x >= 0 && y >= 0 && x < W && y < H && up[(size_t)y * W + x] != 0; };
+        auto D = [&](int x, int y) { return x >= 0 && y >= 0 && x < W && y < H && dn[(size_t)y * W + x] != 0; };
+        lozenge_region((int)W, (int)H, U, D, active, edges);
+    }
+    if (cells == 0 || cells % 2) {
+        delete d;
+        return fail(TL_ENOTTILEABLE, "tl_domain_from_boundary: %lld cells", (long long)cells);
+    }
+    std::vector<int> h;
+    std::string why;
+    const int rc = thurston_heights((int)(W * H), active, edges, top, h, why);
+    if (rc != TL_OK) {
+        delete d;
+        return fail(rc, "tl_domain_from_boundary: %s", why.c_str());
+    }
+    d->init.assign((size_t)d->g.ntype * W * H, 0);
+    tiling_from_heights(edges, h, d->init.data());
     return finish_domain(d, 0, out);
 }
 
@@ -585,9 +875,7 @@ struct tl_chain {
     uint64_t burn = 0;
     bool density_on = false;
     bool counts_dirty = false;         // counters to be zeroed on the next run's stream
-    int* hxlo = nullptr;
-    int* hxhi = nullptr;
-    int* hspine = nullptr;
+    int* hseg = nullptr;
     int* hbase = nullptr;
     int32_t* hscratch = nullptr;
     // planner
@@ -615,9 +903,7 @@ static void chain_free(tl_chain* c)
     cudaFree(c->tplanes);
     cudaFree(c->hash);
     cudaFree(c->counts);
-    cudaFree(c->hxlo);
-    cudaFree(c->hxhi);
-    cudaFree(c->hspine);
+    cudaFree(c->hseg);
     cudaFree(c->hbase);
     cudaFree(c->hscratch);
     cudaFree(c->stripe_d);
@@ -650,12 +936,6 @@ static int dev_alloc(T** p, size_t count, const char* what)
     }
     return TL_OK;
 }
-
-#define TL_TRY(expr)                   \
-    do {                               \
-        int rc_ = (expr);              \
-        if (rc_ != TL_OK) return rc_;  \
-    } while (0)
 
 static int upload_state(tl_chain* c, const uint8_t* canon, bool device_src, void* stream)
 {
@@ -699,17 +979,14 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
         (rc = dev_alloc(&c->rows0, (size_t)g.total_words, "start state")) ||
         (rc = dev_alloc(&c->grange, (size_t)g.H, "group ranges")) ||
         (rc = dev_alloc(&c->canon, ncanon, "staging")) || (rc = dev_alloc(&c->hash, 1, "hash")) ||
-        (rc = dev_alloc(&c->hxlo, (size_t)d->hh, "height plan")) ||
-        (rc = dev_alloc(&c->hxhi, (size_t)d->hh, "height plan")) ||
-        (rc = dev_alloc(&c->hspine, (size_t)d->hh, "height plan")) ||
-        (rc = dev_alloc(&c->hbase, (size_t)d->hh, "height plan"))) {
+        (rc = dev_alloc(&c->hseg, (size_t)6 * std::max(d->nseg, 1), "height plan")) ||
+        (rc = dev_alloc(&c->hbase, (size_t)std::max(d->nseg, 1), "height plan"))) {
         chain_free(c);
         return rc;
     }
     cudaError_t e = cudaMemcpy(c->grange, d->grange.data(), sizeof(int2) * g.H, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->hxlo, d->hxlo.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->hxhi, d->hxhi.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->hspine, d->hspine.data(), sizeof(int) * d->hh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && d->nseg)
+        e = cudaMemcpy(c->hseg, d->hseg.data(), sizeof(int) * 6 * d->nseg, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         chain_free(c);
         return fail(TL_ECUDA, "tl_chain_create: upload: %s", cudaGetErrorString(e));
@@ -1072,7 +1349,7 @@ static int zero_counts_if_needed(tl_chain* c, void* stream)
 TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
 {
     if (!c) return fail(TL_EINVAL, "tl_run_sweeps: NULL chain");
-    if (c->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32");
+    if (c->sweep + k > 0x100000000ull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32 - 1");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     TL_TRY(zero_counts_if_needed(c, stream));
     if (k == 0) return TL_OK;
@@ -1208,6 +1485,75 @@ TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
     return TL_OK;
 }
 
+TL_API int tl_chain_seek(tl_chain* c, uint64_t sweep)
+{
+    if (!c || sweep > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_chain_seek: bad argument");
+    c->sweep = sweep;
+    return TL_OK;
+}
+
+// Coupling from the past (Sec. 1.1.4).  Both chains use the random numbers
+// of the absolute sweeps 2^32 - T .. 2^32 - 1, so when T doubles the last T
+// sweeps repeat exactly the moves of the previous attempt: the run from
+// time -2T first takes T new sweeps and then the old ones.
+TL_API int tl_cftp(tl_ctx* ctx, const tl_domain* d, uint64_t seed, uint32_t stream_id, const tl_thresholds* th,
+                   uint64_t t0, uint64_t tmax, uint8_t* canon_out, size_t cap, uint64_t* t_used, void* stream)
+{
+    if (!ctx || !d || !th || !canon_out || t0 < 1 || tmax < t0 || tmax > 0x80000000ull)
+        return fail(TL_EINVAL, "tl_cftp: bad argument");
+    const size_t n = d->init.size();
+    if (cap < n) return fail(TL_EINVAL, "tl_cftp: cap %zu < %zu", cap, n);
+    std::vector<uint8_t> top_cfg, bot_cfg;
+    TL_TRY(extreme_config(d, true, top_cfg));
+    TL_TRY(extreme_config(d, false, bot_cfg));
+    tl_chain *top = nullptr, *bot = nullptr;
+    int rc = tl_chain_create(ctx, d, top_cfg.data(), seed, stream_id, th, &top);
+    if (rc == TL_OK) rc = tl_chain_create(ctx, d, bot_cfg.data(), seed, stream_id, th, &bot);
+    std::vector<uint8_t> a, b;
+    uint64_t T = t0;
+    bool done = false;
+    while (rc == TL_OK && !done) {
+        for (tl_chain* c : {top, bot}) {
+            if (rc == TL_OK) rc = tl_chain_reset(c, stream);
+            if (rc == TL_OK) rc = tl_chain_seek(c, 0x100000000ull - T);
+            if (rc == TL_OK) rc = tl_run_sweeps(c, T, stream);
+            if (rc == TL_OK) rc = tl_chain_sync(c, stream);
+        }
+        uint64_t ht = 0, hb = 0;
+        if (rc == TL_OK) rc = tl_state_hash(top, &ht, stream);
+        if (rc == TL_OK) rc = tl_state_hash(bot, &hb, stream);
+        if (rc != TL_OK) break;
+        if (ht == hb) {
+            a.resize(n);
+            b.resize(n);
+            rc = tl_read_state(top, a.data(), n, stream);
+            if (rc == TL_OK) rc = tl_read_state(bot, b.data(), n, stream);
+            if (rc == TL_OK && a == b) done = true;
+        }
+        if (!done && rc == TL_OK) {
+            if (T * 2 > tmax) {
+                rc = fail(TL_EBUDGET, "tl_cftp: top and bottom chains still differ after %llu sweeps",
+                          (unsigned long long)T);
+                break;
+            }
+            T *= 2;
+        }
+    }
+    if (rc == TL_OK) {
+        if (is_device_ptr(canon_out)) {
+            cudaSetDevice(ctx->device);
+            const cudaError_t e = cudaMemcpy(canon_out, a.data(), n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = fail(TL_ECUDA, "tl_cftp: %s", cudaGetErrorString(e));
+        } else {
+            std::memcpy(canon_out, a.data(), n);
+        }
+        if (t_used) *t_used = T;
+    }
+    tl_chain_destroy(top);
+    tl_chain_destroy(bot);
+    return rc;
+}
+
 TL_API int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream)
 {
     if (!c || !out) return fail(TL_EINVAL, "tl_read_height: NULL argument");
@@ -1221,9 +1567,9 @@ TL_API int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream)
         if (!c->hscratch) TL_TRY(dev_alloc(&c->hscratch, n, "height scratch"));
         dst = c->hscratch;
     }
-    const int e = launch_height(c->g, c->rows, c->hxlo, c->hxhi, c->hspine, d.hw, d.hh, dst, c->hbase, stream);
+    const int e = launch_height(c->g, c->rows, c->hseg, d.nseg, d.hw, d.hh, dst, c->hbase, stream);
     if (e) return fail(TL_ECUDA, "height kernels: %s", cudaGetErrorString((cudaError_t)e));
-    c->launches += 3;
+    c->launches += d.nseg ? 4 : 1;
     if (!dev) {
         CUDA_TRY(cudaMemcpyAsync(out, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, SS(stream)));
         CUDA_TRY(cudaStreamSynchronize(SS(stream)));
@@ -1237,17 +1583,16 @@ TL_API int tl_read_height_noalloc(tl_chain* c, int32_t* out, size_t cap, void* s
     const tl_domain& d = c->dom_copy;
     const size_t n = (size_t)d.hw * d.hh;
     if (cap < n) return fail(TL_EINVAL, "tl_read_height_noalloc: cap %zu < %zu", cap, n);
-    if (d.hh > noalloc_height_max_rows())
-        return fail(TL_EINVAL, "tl_read_height_noalloc: %d height rows exceed the static scratch limit of %d",
-                    d.hh, noalloc_height_max_rows());
+    if (d.nseg > noalloc_height_max_rows())
+        return fail(TL_EINVAL, "tl_read_height_noalloc: %d height segments exceed the static scratch limit of %d",
+                    d.nseg, noalloc_height_max_rows());
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     if (!is_device_ptr(out))
         return fail(TL_EINVAL, "tl_read_height_noalloc: `out` must be device memory (a host buffer would "
                                "need a staging allocation)");
-    const int e = launch_height_noalloc(c->g, c->rows, c->hxlo, c->hxhi, c->hspine, d.hw, d.hh, out,
-                                        c->ctx->device, stream);
+    const int e = launch_height_noalloc(c->g, c->rows, c->hseg, d.nseg, d.hw, d.hh, out, c->ctx->device, stream);
     if (e) return fail(TL_ECUDA, "tl_read_height_noalloc: %s", cudaGetErrorString((cudaError_t)e));
-    c->launches += 3;
+    c->launches += d.nseg ? 4 : 1;
     return TL_OK;
 }
 

@@ -72,17 +72,17 @@ int launch_density_read(const uint32_t* counts, uint64_t n, uint64_t samples, do
                         void* stream);
 int launch_nsew(const Geom& g, const uint32_t* counts, uint64_t samples, int kappa, double* out,
                 void* stream);
-int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi,
-                  const int* spine, int hw, int hh, int32_t* out, int* base_scratch,
-                  void* stream);
+// seg: [nseg][6] height segments (y, lo, hi, parent, xs, dir); base_scratch: nseg ints.
+int launch_height(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
+                  int32_t* out, int* base_scratch, void* stream);
 int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t* planes,
                             void* stream);
 // Device-generated log-normal weights -> per-site thresholds [H][W].
 int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_t seed, uint32_t* t, void* stream);
-// Height with its row-offset scratch in a static device array (no allocation).
+// Height with its segment-offset scratch in a static device array (no allocation).
 int noalloc_height_max_rows();
-int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,
-                          int hw, int hh, int32_t* out, int device, void* stream);
+int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
+                          int32_t* out, int device, void* stream);
 
 // Resident multi-sweep kernel.  One cooperative launch runs `nsweeps`
 // sweeps from absolute sweep `sweep0`.  CTA c owns the rows

@@ -277,9 +277,9 @@ int launch_nsew(const Geom& g, const uint32_t* counts, uint64_t samples, int kap
     return (int)cudaGetLastError();
 }
 
-// Height function: (1) per-row prefix sums of horizontal steps over the
-// row's domain interval, (2) one block links the rows along their spine
-// columns and scans the row offsets, (3) offsets are added.
+// Height function: (1) prefix sums of horizontal steps along each segment
+// of a row, (2) one block links every segment to its parent through a
+// vertical step and accumulates the offsets, (3) offsets are added.
 TL_DEV uint32_t bit_at(const uint32_t* rows0, const Geom& g, int type, int x, int y)
 {
     if (x < 0 || y < 0 || x >= g.W || y >= g.H) return 0u;
@@ -308,16 +308,27 @@ TL_DEV int vstep(const uint32_t* rows0, const Geom& g, int x, int y)
     return bit_at(rows0, g, 0, x, y) ? 1 : -1;       // faces: cross Hz(x, y)
 }
 
-__global__ void __launch_bounds__(256) height_rows_kernel(const uint32_t* __restrict__ rows0, Geom g,
-                                                          const int* __restrict__ xlo,
-                                                          const int* __restrict__ xhi, int hw,
-                                                          int32_t* __restrict__ out)
+// Height segments: seg[6 s .. 6 s + 5] = (y, lo, hi, parent, xs, dir): a
+// maximal run [lo, hi] of row y joined by domain steps, the segment it is
+// linked to (-1 for the first, which holds the reference vertex) and the
+// column xs of the linking vertical step, dir = +1 if this segment lies one
+// row above its parent and -1 if below.  Parents precede children.
+__global__ void height_fill_kernel(int32_t* __restrict__ out, int64_t n)
 {
-    const int y = blockIdx.x;
-    const int lo = xlo[y], hi = xhi[y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = INT32_MIN;
+}
+
+// Heights along each segment relative to its left end.
+__global__ void __launch_bounds__(256) height_seg_kernel(const uint32_t* __restrict__ rows0, Geom g,
+                                                         const int* __restrict__ seg, int hw,
+                                                         int32_t* __restrict__ out)
+{
+    const int* sg = seg + 6 * (size_t)blockIdx.x;
+    const int y = sg[0], lo = sg[1], hi = sg[2];
     int32_t* o = out + (size_t)y * hw;
     __shared__ int part[256];
-    const int n = hi >= lo ? hi - lo + 1 : 0;
+    const int n = hi - lo + 1;
     const int per = (n + 255) / 256;
     const int a = lo + threadIdx.x * per;
     int sum = 0;
@@ -341,62 +352,64 @@ __global__ void __launch_bounds__(256) height_rows_kernel(const uint32_t* __rest
             if (x < hi) run += hstep(rows0, g, x, y);
         }
     }
-    for (int x = threadIdx.x; x < hw; x += 256)
-        if (x < lo || x > hi) o[x] = INT32_MIN;
 }
 
-__global__ void __launch_bounds__(1024) height_base_kernel(const uint32_t* __restrict__ rows0, Geom g,
-                                                           const int* __restrict__ xlo,
-                                                           const int* __restrict__ xhi,
-                                                           const int* __restrict__ spine, int hw,
-                                                           int hh, const int32_t* __restrict__ rel,
-                                                           int* __restrict__ base)
+// Offsets of the segments: the differences to the parents in parallel, then
+// one thread accumulates them in parent-first order.
+__global__ void __launch_bounds__(1024) height_link_kernel(const uint32_t* __restrict__ rows0, Geom g,
+                                                           const int* __restrict__ seg, int nseg, int hw,
+                                                           const int32_t* __restrict__ rel, int* __restrict__ base)
 {
-    // base[y] - base[prev] along the spine column xs = spine[y]
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    __shared__ int part[1024];
-    for (int c0 = 0; c0 < hh; c0 += 1024) {
-        const int y = c0 + threadIdx.x;
-        int d = 0;
-        if (y < hh && xlo[y] <= xhi[y] && spine[y] >= 0) {
-            const int xs = spine[y];
-            // previous non-empty row is y-1 (rows of the built-in domains are contiguous)
-            d = rel[(size_t)(y - 1) * hw + xs] + vstep(rows0, g, xs, y) - rel[(size_t)y * hw + xs];
+    __shared__ int dd[1024], par[1024];
+    int last = 0;
+    for (int c0 = 0; c0 < nseg; c0 += 1024) {
+        const int s = c0 + threadIdx.x;
+        if (s < nseg) {
+            const int* sg = seg + 6 * (size_t)s;
+            const int y = sg[0], p = sg[3], xs = sg[4], dir = sg[5];
+            int d = 0;
+            if (p >= 0) {
+                const int py = seg[6 * (size_t)p];
+                const int step = dir > 0 ? vstep(rows0, g, xs, y) : -vstep(rows0, g, xs, y + 1);
+                d = rel[(size_t)py * hw + xs] + step - rel[(size_t)y * hw + xs];
+            }
+            dd[threadIdx.x] = d;
+            par[threadIdx.x] = p;
         }
-        part[threadIdx.x] = d;
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += v;
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            const int n = nseg - c0 < 1024 ? nseg - c0 : 1024;
+            for (int i = 0; i < n; ++i) {
+                const int s2 = c0 + i, p = par[i];
+                const int b = p < 0 ? 0 : (p == s2 - 1 ? last : base[p]);
+                last = b + dd[i];
+                base[s2] = last;
+            }
         }
-        if (y < hh) base[y] = carry + part[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
         __syncthreads();
     }
 }
 
-__global__ void height_add_kernel(int32_t* __restrict__ out, const int* __restrict__ base, int hw, int hh)
+__global__ void __launch_bounds__(256) height_add_kernel(int32_t* __restrict__ out, const int* __restrict__ seg,
+                                                         const int* __restrict__ base, int hw)
 {
-    const int64_t n = (int64_t)hw * hh;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = out[i];
-        if (v != INT32_MIN) out[i] = v + base[i / hw];
-    }
+    const int* sg = seg + 6 * (size_t)blockIdx.x;
+    const int y = sg[0], lo = sg[1], hi = sg[2];
+    const int b = base[blockIdx.x];
+    int32_t* o = out + (size_t)y * hw;
+    for (int x = lo + threadIdx.x; x <= hi; x += 256) o[x] += b;
 }
 
-int launch_height(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,
-                  int hw, int hh, int32_t* out, int* base_scratch, void* stream)
+int launch_height(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh, int32_t* out,
+                  int* base_scratch, void* stream)
 {
     const uint32_t* rows0 = rows + g.row_words;
-    height_rows_kernel<<<hh, 256, 0, S(stream)>>>(rows0, g, xlo, xhi, hw, out);
-    height_base_kernel<<<1, 1024, 0, S(stream)>>>(rows0, g, xlo, xhi, spine, hw, hh, out, base_scratch);
-    height_add_kernel<<<grid_for((int64_t)hw * hh, 256), 256, 0, S(stream)>>>(out, base_scratch, hw, hh);
+    height_fill_kernel<<<grid_for((int64_t)hw * hh, 256), 256, 0, S(stream)>>>(out, (int64_t)hw * hh);
+    if (nseg > 0) {
+        height_seg_kernel<<<nseg, 256, 0, S(stream)>>>(rows0, g, seg, hw, out);
+        height_link_kernel<<<1, 1024, 0, S(stream)>>>(rows0, g, seg, nseg, hw, out, base_scratch);
+        height_add_kernel<<<nseg, 256, 0, S(stream)>>>(out, seg, base_scratch, hw);
+    }
     return (int)cudaGetLastError();
 }
 
@@ -470,7 +483,7 @@ int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_
 // device memory at the time they need the heights (for example code running
 // under a memory budget that forbids cudaMalloc, or a real-time loop that
 // must not synchronise the device the way cudaMalloc / cudaFree can), the
-// per-row offsets that launch_height keeps in chain-owned memory live here
+// per-segment offsets that launch_height keeps in chain-owned memory live here
 // in one file-scope device array instead.  The array holds kNoAllocMaxRows
 // ints (256 KiB), enough for any box this library accepts (at most 65536
 // rows); every GPU that loads the library keeps it until the process exits.
@@ -504,14 +517,14 @@ static int noalloc_scratch(int device, int** out)
     return 0;
 }
 
-int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* xlo, const int* xhi, const int* spine,
-                          int hw, int hh, int32_t* out, int device, void* stream)
+int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
+                          int32_t* out, int device, void* stream)
 {
-    if (hh > kNoAllocMaxRows) return (int)cudaErrorInvalidValue;
+    if (nseg > kNoAllocMaxRows) return (int)cudaErrorInvalidValue;
     int* base = nullptr;
     const int e = noalloc_scratch(device, &base);
     if (e) return e;
-    return launch_height(g, rows, xlo, xhi, spine, hw, hh, out, base, stream);
+    return launch_height(g, rows, seg, nseg, hw, hh, out, base, stream);
 }
 
 }  // namespace tl

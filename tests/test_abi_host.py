@@ -125,3 +125,101 @@ def test_sixv_thresholds_bit_exact(T):
         assert np.array_equal(T.sixv_thresholds(w6), O.sixv_thresholds(w6))
     with pytest.raises(T.TilingError):
         T.sixv_thresholds([1, 1, 0, 1, 1, 1])
+
+
+# ---------------------------------------------------------------------------
+# Extreme configurations and domains from a boundary path (host code)
+# ---------------------------------------------------------------------------
+def _builtin(T, kind, args):
+    dom = {"aztec": T.Domain.aztec, "rect": T.Domain.rect, "hex": T.Domain.hexagon,
+           "dwbc": T.Domain.dwbc}[kind](*args)
+    st = {"aztec": O.aztec, "rect": O.rect, "hex": O.hexagon, "dwbc": O.dwbc}[kind](*args)
+    lat = {"aztec": O.DOMINO, "rect": O.DOMINO, "hex": O.LOZENGE, "dwbc": O.SIXV}[kind]
+    return dom, st, lat
+
+
+@pytest.mark.parametrize("kind,args", [("aztec", (1,)), ("aztec", (2,)), ("aztec", (5,)), ("aztec", (12,)),
+                                       ("rect", (6, 5)), ("rect", (7, 4)), ("hex", (1, 1, 1)),
+                                       ("hex", (3, 5, 4)), ("hex", (6, 2, 7)), ("dwbc", (2,)),
+                                       ("dwbc", (7,)), ("dwbc", (16,))])
+def test_extreme_states_match_oracle(T, kind, args):
+    # Thurston's extreme tilings (host, product) against the oracle's pointwise
+    # height pushes from its own starting tiling
+    dom, st, lat = _builtin(T, kind, args)
+    assert np.array_equal(dom.extreme_state("top"), O.extreme(lat, st, True))
+    assert np.array_equal(dom.extreme_state("bottom"), O.extreme(lat, st, False))
+
+
+def _shapes():
+    sys_path = os.path.join(ROOT, "tests")
+    import sys
+    if sys_path not in sys.path:
+        sys.path.insert(0, sys_path)
+    from test_oracle_pins import DOMINO_SHAPES, _aztec_path
+    shapes = dict(DOMINO_SHAPES)
+    shapes["aztec9"] = _aztec_path(9)
+    # a spiral corridor of width 2 (many segments per row)
+    shapes["zigzag"] = ([0] * 8 + [1] * 2 + [2] * 6 + [1] * 2 + [0] * 6 + [1] * 2 + [2] * 8 + [3] * 6)
+    return shapes
+
+
+@pytest.mark.parametrize("name", ["square4", "L", "U", "aztec4", "aztec9", "zigzag"])
+def test_domino_from_boundary_matches_oracle(T, name):
+    steps = _shapes()[name]
+    reg = O.region_from_boundary(O.DOMINO, steps)
+    dom = T.Domain.from_boundary(T.DOMINO, steps)
+    face, W, H = reg
+    assert dom.canon_shape == (2, H, W)
+    ost = O.tiling_by_search(O.DOMINO, reg)
+    assert np.array_equal(dom.initial_state(), O.extreme(O.DOMINO, ost, False))
+    assert np.array_equal(dom.extreme_state("top"), O.extreme(O.DOMINO, ost, True))
+
+
+def test_aztec_boundary_gives_the_aztec_domain(T):
+    _shapes()   # puts tests/ on the path
+    from test_oracle_pins import _aztec_path
+    for n in (3, 8):
+        dom = T.Domain.from_boundary(T.DOMINO, _aztec_path(n))
+        ref = T.Domain.aztec(n)
+        assert dom.info.sites == ref.info.sites and dom.info.edges == ref.info.edges
+        assert np.array_equal(dom.initial_state(), ref.extreme_state("bottom"))
+
+
+LOZENGE_SHAPES = {
+    "hex213": [0] * 2 + [2] * 1 + [1] * 3 + [3] * 2 + [5] * 1 + [4] * 3,
+    "hex444": [0] * 4 + [2] * 4 + [1] * 4 + [3] * 4 + [5] * 4 + [4] * 4,
+    # hexagon with a notch: non-convex rows
+    "notched": [0] * 4 + [2] * 2 + [1] * 3 + [3] * 1 + [4] * 1 + [3] * 1 + [1] * 1 + [3] * 2
+               + [5] * 2 + [4] * 3,
+}
+
+
+@pytest.mark.parametrize("name", sorted(LOZENGE_SHAPES))
+def test_lozenge_from_boundary_matches_oracle(T, name):
+    steps = LOZENGE_SHAPES[name]
+    reg = O.region_from_boundary(O.LOZENGE, steps)
+    ost = O.tiling_by_search(O.LOZENGE, reg)
+    if ost is None:
+        with pytest.raises(T.TilingError) as e:
+            T.Domain.from_boundary(T.LOZENGE, steps)
+        assert e.value.code == T.TL_ENOTTILEABLE
+        return
+    dom = T.Domain.from_boundary(T.LOZENGE, steps)
+    assert np.array_equal(dom.initial_state(), O.extreme(O.LOZENGE, ost, False))
+    assert np.array_equal(dom.extreme_state("top"), O.extreme(O.LOZENGE, ost, True))
+
+
+def test_from_boundary_errors(T):
+    cases = [
+        (T.DOMINO, [0] * 3 + [1] * 3 + [2] * 3 + [3] * 3, T.TL_ENOTTILEABLE),        # odd area
+        (T.DOMINO, [0] * 3 + [1] * 3 + [2] + [1] + [2] * 3 + [3] * 3 + [0] + [3],
+         T.TL_ENOTTILEABLE),                                                     # two opposite corners cut
+        (T.DOMINO, [0, 0, 1, 1, 2, 2], T.TL_EINVAL),                                # not closed
+        (T.DOMINO, [0, 0, 1, 2, 3, 2, 1, 1, 0, 3, 3, 2], T.TL_ENOTSIMPLY),          # revisits a point
+        (T.DOMINO, [0, 5, 2, 3], T.TL_EINVAL),                                      # bad step code
+        (T.SIXV, [0, 1, 2, 3], T.TL_EINVAL),                                        # lattice without paths
+    ]
+    for lat, steps, code in cases:
+        with pytest.raises(T.TilingError) as e:
+            T.Domain.from_boundary(lat, steps)
+        assert e.value.code == code, (steps, e.value)

@@ -1,0 +1,130 @@
+"""GPU parity on domains given by a boundary path, and coupling from the past.
+
+Domains from a closed lattice path (Sec. 1.1) may have rows made of several
+runs of sites; the sweeps and the height integration must handle them.  The
+oracle builds the region from the same path by itself and finds a tiling by
+search; the chain starts from that tiling on both sides.
+
+Coupling from the past (Sec. 1.1.4): the library's exact sample and the
+number of sweeps it needed must equal the oracle's, which runs the same
+negative-time schedule from its own extreme tilings.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SQ2 = [1, 1, 1, 1, math.sqrt(2), math.sqrt(2)]
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_07250_gb300 as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.Context(0)
+
+
+def _comb(width, tooth, gap, teeth, base):
+    """Domino path of a comb: a base of `base` rows and `teeth` teeth of width
+    `tooth` and height `gap`... every row above the base holds many runs."""
+    steps = [0] * width + [1] * base
+    x = width
+    pitch = (width - tooth) // max(teeth - 1, 1)
+    for i in range(teeth):
+        xr = width - i * pitch          # right edge of tooth i
+        steps += [2] * (x - xr)         # along the top of the base (or nothing)
+        steps += [1] * gap + [2] * tooth + [3] * gap
+        x = xr - tooth
+    steps += [2] * x + [3] * base
+    return steps
+
+
+DOMINO_PATHS = {
+    "comb": lambda: _comb(width=300, tooth=6, gap=21, teeth=12, base=10),
+    "U": lambda: [0] * 290 + [1] * 40 + [2] * 40 + [3] * 30 + [2] * 210 + [1] * 30 + [2] * 40 + [3] * 40,
+}
+
+
+@pytest.mark.parametrize("name", sorted(DOMINO_PATHS))
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_domino_region_parity(T, ctx, name, kernel):
+    steps = DOMINO_PATHS[name]()
+    reg = O.region_from_boundary(O.DOMINO, steps)
+    st = O.tiling_by_search(O.DOMINO, reg)
+    assert st is not None
+    dom = T.Domain.from_boundary(T.DOMINO, steps)
+    ch = T.Chain(ctx, dom, seed=21, stream_id=4, th=T.thresholds(scalar=0x6A09E667), init=st)
+    ch.set_plan(kernel)
+    ring = ch.run_hashed(25)
+    ohash = O.sweeps(O.DOMINO, st, seed=21, stream=4, k=25, t_scalar=0x6A09E667, want_hashes=True)
+    assert np.array_equal(ring, ohash)
+    assert np.array_equal(ch.read_state(), st)
+    h, bad = O.height(O.DOMINO, st)
+    assert bad == 0
+    assert np.array_equal(ch.read_height(), h)
+
+
+def test_lozenge_region_parity(T, ctx):
+    # a large hexagon with a rectangular notch cut into its upper side
+    a, b, c = 150, 60, 70
+    steps = [0] * a + [2] * b + [1] * c + [3] * 40 + [4] * 30 + [3] * 30 + [1] * 30 + [3] * (a - 70) \
+        + [5] * b + [4] * c
+    reg = O.region_from_boundary(O.LOZENGE, steps)
+    st = O.tiling_by_search(O.LOZENGE, reg)
+    assert st is not None
+    dom = T.Domain.from_boundary(T.LOZENGE, steps)
+    ta, _ = O.lozenge_thresholds(0.97)
+    ch = T.Chain(ctx, dom, seed=5, stream_id=2, th=T.thresholds(scalar=ta), init=st)
+    ring = ch.run_hashed(20)
+    ohash = O.sweeps(O.LOZENGE, st, seed=5, stream=2, k=20, t_scalar=ta, want_hashes=True)
+    assert np.array_equal(ring, ohash)
+    h, bad = O.height(O.LOZENGE, st)
+    assert bad == 0
+    assert np.array_equal(ch.read_height(), h)
+
+
+@pytest.mark.parametrize("case", ["aztec10", "aztec17", "hex546", "dwbc9", "region_U"])
+def test_cftp_matches_oracle(T, ctx, case):
+    if case.startswith("aztec"):
+        n = int(case[5:])
+        dom, st0, lat = T.Domain.aztec(n), O.aztec(n), O.DOMINO
+        th, okw = T.thresholds(scalar=1 << 31), dict(t_scalar=1 << 31)
+    elif case == "hex546":
+        dom, st0, lat = T.Domain.hexagon(5, 4, 6), O.hexagon(5, 4, 6), O.LOZENGE
+        ta, _ = O.lozenge_thresholds(0.8)
+        th, okw = T.thresholds(scalar=ta), dict(t_scalar=ta)
+    elif case == "dwbc9":
+        dom, st0, lat = T.Domain.dwbc(9), O.dwbc(9), O.SIXV
+        t16 = O.sixv_thresholds(SQ2)
+        th, okw = T.thresholds(table16=t16), dict(t16=t16)
+    else:
+        steps = [0] * 12 + [1] * 10 + [2] * 4 + [3] * 6 + [2] * 4 + [1] * 6 + [2] * 4 + [3] * 10
+        reg = O.region_from_boundary(O.DOMINO, steps)
+        st0, lat = O.tiling_by_search(O.DOMINO, reg), O.DOMINO
+        dom = T.Domain.from_boundary(T.DOMINO, steps)
+        th, okw = T.thresholds(scalar=0x50000000), dict(t_scalar=0x50000000)
+    top, bot = O.extreme(lat, st0, True), O.extreme(lat, st0, False)
+    want, T_o = O.cftp(lat, top, bot, seed=77, stream=3, t0=4, **okw)
+    got, T_g = T.cftp(ctx, dom, seed=77, stream_id=3, th=th, t0=4)
+    assert T_g == T_o
+    assert np.array_equal(got, want)
+
+
+def test_cftp_gives_up_at_tmax(T, ctx):
+    dom = T.Domain.aztec(30)
+    with pytest.raises(T.TilingError) as e:
+        T.cftp(ctx, dom, seed=1, th=T.thresholds(scalar=1 << 31), t0=1, tmax=4)
+    assert e.value.code == T.TL_EBUDGET

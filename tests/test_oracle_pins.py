@@ -601,3 +601,129 @@ def test_sixv_flip_raises_face_height_by_two():
     assert np.array_equal(h[:, 0], ar)          # left externals occupied
     assert np.array_equal(h[N, :], N - ar)      # top externals empty
     assert np.array_equal(h[:, N], N - ar)      # right externals empty
+
+
+# ---------------------------------------------------------------------------
+# Extreme tilings, regions from a boundary path, coupling from the past
+# (Sec. 1.1 T_max / T_min and Thurston's algorithm; Sec. 1.1.4)
+# ---------------------------------------------------------------------------
+def _enum_case(case):
+    if case == "aztec3":
+        return O.DOMINO, O.aztec(3)
+    if case == "rect4x3":
+        return O.DOMINO, O.rect(4, 3)
+    if case == "hex223":
+        return O.LOZENGE, O.hexagon(2, 2, 3)
+    return O.SIXV, O.dwbc(4)
+
+
+@pytest.mark.parametrize("case", ["aztec3", "rect4x3", "hex223", "dwbc4"])
+def test_extremes_bound_every_tiling(case):
+    # T_max / T_min are the pointwise largest / smallest height functions
+    # among all tilings of the domain (enumerated by elementary moves)
+    lat, st0 = _enum_case(case)
+    states, _ = enumerate_states(lat, st0)
+    hs = np.stack([O.height(lat, s)[0] for s in states])
+    hmax, hmin = hs.max(axis=0), hs.min(axis=0)
+    top, bot = O.extreme(lat, st0, True), O.extreme(lat, st0, False)
+    assert np.array_equal(O.height(lat, top)[0], hmax)
+    assert np.array_equal(O.height(lat, bot)[0], hmin)
+
+
+def _aztec_path(n):
+    # boundary of the Aztec diamond of order n, counter-clockwise from the
+    # lower end of its left column of faces: staircases of unit steps
+    steps = []
+    for _ in range(n):
+        steps += [3, 0]          # down-right staircase (lower left edge)
+    for _ in range(n):
+        steps += [0, 1]          # up-right (lower right edge)
+    for _ in range(n):
+        steps += [1, 2]          # up-left (upper right edge)
+    for _ in range(n):
+        steps += [2, 3]          # down-left (upper left edge)
+    return steps
+
+
+DOMINO_SHAPES = {
+    "square4": [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4,
+    "L": [0] * 4 + [1] * 2 + [2] * 2 + [1] * 2 + [2] * 2 + [3] * 4,
+    "U": [0] * 6 + [1] * 4 + [2] * 2 + [3] * 2 + [2] * 2 + [1] * 2 + [2] * 2 + [3] * 4,
+    "aztec4": _aztec_path(4),
+}
+
+
+def test_region_cells_and_search_tilings():
+    face, W, H = O.region_from_boundary(O.DOMINO, DOMINO_SHAPES["square4"])
+    assert face.sum() == 16 and (W, H) == (5, 5)
+    face, W, H = O.region_from_boundary(O.DOMINO, DOMINO_SHAPES["U"])
+    assert face.sum() == 20
+    assert not face[2, 2] and not face[3, 3] and face[1, 2]
+    face, W, H = O.region_from_boundary(O.DOMINO, _aztec_path(4))
+    assert np.array_equal(face, _aztec_faces(4))
+    for name, steps in DOMINO_SHAPES.items():
+        reg = O.region_from_boundary(O.DOMINO, steps)
+        st = O.tiling_by_search(O.DOMINO, reg)
+        assert st is not None and O.domino_check(st, reg[0]) == 0, name
+    # hexagon with sides (a, b, c) along +x, +x+y, +y: 2(ab + bc + ca) triangles,
+    # and its tilings by search count like MacMahon's box
+    a, b, c = 2, 1, 2
+    steps = [0] * a + [2] * b + [1] * c + [3] * a + [5] * b + [4] * c
+    up, dn, W, H = O.region_from_boundary(O.LOZENGE, steps)
+    assert up.sum() + dn.sum() == 2 * (a * b + b * c + c * a)
+    st = O.tiling_by_search(O.LOZENGE, (up, dn, W, H))
+    assert st is not None and O.lozenge_check(st, up, dn) == 0
+    states, _ = enumerate_states(O.LOZENGE, st)
+    # MacMahon: prod over the box of (i+j+k-1)/(i+j+k-2) = 2 * 3/2 * 3/2 * 4/3 = 6
+    assert len(states) == 6
+
+
+def test_search_finds_no_tiling_of_untileable_regions():
+    # 4 x 4 square without two opposite corners (same colour): no tiling
+    steps = [0] * 3 + [1] * 3 + [2] + [1] + [2] * 3 + [3] * 3 + [0] + [3]
+    reg = O.region_from_boundary(O.DOMINO, steps)
+    assert reg[0].sum() == 14
+    assert O.tiling_by_search(O.DOMINO, reg) is None
+
+
+@pytest.mark.parametrize("case", ["aztec2", "hex222", "dwbc3"])
+def test_cftp_samples_exactly(case):
+    # coupling from the past returns exact samples: chi-square of the outputs
+    # over independent seeds against the Gibbs law
+    if case == "aztec2":
+        lat, st0, kw = O.DOMINO, O.aztec(2), dict(t_scalar=1 << 31)
+        states, index = enumerate_states(lat, st0)
+        pi = np.ones(len(states))
+    elif case == "hex222":
+        lat, st0 = O.LOZENGE, O.hexagon(2, 2, 2)
+        ta, _ = O.lozenge_thresholds(1.5)
+        kw = dict(t_scalar=ta)
+        h0, _ = O.height(O.LOZENGE, st0)
+        states, index = enumerate_states(lat, st0)
+        pi = np.array([1.5 ** _volume(s, h0) for s in states])
+    else:
+        lat, st0 = O.SIXV, O.dwbc(3)
+        w6 = [1, 1, 1, 1, math.sqrt(2), math.sqrt(2)]
+        kw = dict(t16=O.sixv_thresholds(w6))
+        states, index = enumerate_states(lat, st0)
+        pi = np.array([O.sixv_weight(s, w6) for s in states])
+    pi = pi / pi.sum()
+    top, bot = O.extreme(lat, st0, True), O.extreme(lat, st0, False)
+    counts = np.zeros(len(states))
+    for seed in range(600):
+        s, T = O.cftp(lat, top, bot, seed=seed, stream=7, t0=2, **kw)
+        counts[index[s.tobytes()]] += 1
+    assert _chi2_pvalue(counts, pi) > 1e-4
+
+
+def test_coupled_chains_stay_ordered():
+    # the heat-bath move with shared random numbers is monotone: the chain
+    # from T_max stays pointwise above the chain from T_min at every sweep
+    for lat, st0, kw in ((O.DOMINO, O.aztec(5), dict(t_scalar=0x70000000)),
+                         (O.LOZENGE, O.hexagon(3, 4, 2), dict(t_scalar=0x9000_0000)),
+                         (O.SIXV, O.dwbc(6), dict(t16=O.sixv_thresholds([1, 1, 1, 1, 1.7, 1.7])))):
+        a, b = O.extreme(lat, st0, True), O.extreme(lat, st0, False)
+        for s in range(40):
+            O.sweeps(lat, a, seed=9, sweep0=s, k=1, **kw)
+            O.sweeps(lat, b, seed=9, sweep0=s, k=1, **kw)
+            assert np.all(O.height(lat, a)[0] >= O.height(lat, b)[0]), (lat, s)
