@@ -197,6 +197,18 @@ int tl_domain_from_boundary(int lattice, const int8_t* steps, size_t nsteps, tl_
 int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w, size_t n_w,
                                       uint32_t* t, size_t n_t);
 
+/* Volume weights (Sec. 1.1.1: W(T) = prod over vertices of q_v^{h_T(v)};
+ * for lozenges the height is the cube-stack height, so q_v weighs each cube
+ * stacked at v).  `q` is [H][W] doubles, one per box vertex (n_q = W*H).
+ * A domino rotation at (x,y) changes only h(x,y), by 4; UP raises it when
+ * x + y is even and lowers it when odd (Fig. 2 with h = 0 at the first
+ * domain vertex), so with q4 = (q*q)*(q*q): P = q4 / (1 + q4) for x + y
+ * even and 1 / (1 + q4) for x + y odd.  Lozenges: P(add) = q / (1 + q).
+ * Output t[y][x] (n_t = W*H) for use as per-site thresholds.  Errors:
+ * TL_EINVAL (six-vertex domain, size mismatch, q outside [1e-75, 1e75],
+ * where q^4 would leave the normal doubles). */
+int tl_thresholds_volume(const tl_domain* d, const double* q, size_t n_q, uint32_t* t, size_t n_t);
+
 /* Generated log-normal weights (weight = exp(sigma Z), Z standard normal),
  * drawn on the device from Philox4x32-10 keyed by `seed` and the canonical
  * index of each edge (dominoes: dual-edge weights, thresholds as in

@@ -231,6 +231,36 @@ def domino_thresholds(w: np.ndarray) -> np.ndarray:
     return t
 
 
+def volume_thresholds(lattice: str, q: np.ndarray) -> np.ndarray:
+    """Heat-bath thresholds for volume weights (Sec. 1.1.1): the Gibbs weight
+    is prod_v q_v^h(v).  A domino rotation at v moves h(v) by 4, upward for
+    UP exactly when x + y is even (by the Fig. 2 rule: the block's east edge
+    has the black square on its left then); a lozenge UP adds one cube.
+    P(UP) = q^4 / (1 + q^4) or 1 / (1 + q^4) (dominoes), q / (1 + q)
+    (lozenges); t = min(floor(2^32 P), 2^32 - 1)."""
+    q = np.asarray(q, dtype=np.float64)
+    H, W = q.shape
+    t = np.zeros((H, W), dtype=np.uint32)
+    for y in range(H):
+        for x in range(W):
+            qv = float(q[y, x])
+            if lattice == DOMINO:
+                q4 = (qv * qv) * (qv * qv)
+                p = q4 / (1.0 + q4) if (x + y) % 2 == 0 else 1.0 / (1.0 + q4)
+            else:
+                p = qv / (1.0 + qv)
+            t[y, x] = min(int(np.floor(p * 4294967296.0)), 0xFFFFFFFF)
+    return t
+
+
+def volume_weight(lattice: str, st: np.ndarray, q: np.ndarray) -> float:
+    """prod_v q_v^h(v) over the domain's vertices (Sec. 1.1.1)."""
+    h, bad = height(lattice, st)
+    assert bad == 0
+    m = h != HEIGHT_NONE
+    return float(np.prod(np.asarray(q, dtype=np.float64)[m] ** h[m].astype(np.float64)))
+
+
 def domino_weight(st: np.ndarray, w: np.ndarray) -> float:
     w = np.ascontiguousarray(w, dtype=np.float64)
     _, H, W = st.shape

@@ -90,6 +90,7 @@ _SIG = {
     "tl_domain_from_boundary": (_i, [_i, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "tl_thresholds_domino_edge_weights": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]),
     "tl_thresholds_lozenge_q": (_i, [ctypes.c_double, _vp, _vp]),
+    "tl_thresholds_volume": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]),
     "tl_thresholds_lognormal_device": (_i, [_vp, ctypes.c_double, _u64, _vp, ctypes.c_size_t, _vp]),
     "tl_thresholds_6v": (_i, [_vp, _vp]),
     "tl_chain_create": (_i, [_vp, _vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds),
@@ -245,6 +246,15 @@ class Domain:
         pw, _ = _ptr(w)
         pt, _ = _ptr(t)
         _check(_lib.tl_thresholds_domino_edge_weights(self._h, pw, w.size, pt, t.size))
+        return t
+
+    def volume_thresholds(self, q: np.ndarray) -> np.ndarray:
+        """Per-site thresholds from volume weights q[H, W] (one per box vertex)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        t = np.zeros((self.info.height, self.info.width), dtype=np.uint32)
+        pq, _ = _ptr(q)
+        pt, _ = _ptr(t)
+        _check(_lib.tl_thresholds_volume(self._h, pq, q.size, pt, t.size))
         return t
 
     def lognormal_thresholds_device(self, sigma: float, seed: int, out, stream=None):

@@ -795,6 +795,31 @@ TL_API int tl_thresholds_domino_edge_weights(const tl_domain* d, const double* w
     return TL_OK;
 }
 
+TL_API int tl_thresholds_volume(const tl_domain* d, const double* q, size_t n_q, uint32_t* t, size_t n_t)
+{
+    if (!d || !q || !t) return fail(TL_EINVAL, "volume thresholds: NULL argument");
+    if (d->g.lattice == LAT_SIXV) return fail(TL_EINVAL, "volume thresholds: six-vertex uses tl_thresholds_6v");
+    const int W = d->g.W, H = d->g.H;
+    if (n_q != (size_t)W * H || n_t != (size_t)W * H)
+        return fail(TL_EINVAL, "volume thresholds: sizes %zu/%zu, want %zu", n_q, n_t, (size_t)W * H);
+    for (size_t i = 0; i < n_q; ++i)
+        if (!(q[i] >= 1e-75 && q[i] <= 1e75))   // q^4 stays a normal double
+            return fail(TL_EINVAL, "volume thresholds: q[%zu] = %g outside [1e-75, 1e75]", i, q[i]);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double qv = q[(size_t)y * W + x];
+            double p;
+            if (d->g.lattice == LAT_DOMINO) {
+                const double q4 = (qv * qv) * (qv * qv);
+                p = ((x + y) & 1) == 0 ? q4 / (1.0 + q4) : 1.0 / (1.0 + q4);
+            } else {
+                p = qv / (1.0 + qv);
+            }
+            t[(size_t)y * W + x] = to_threshold(p);
+        }
+    return TL_OK;
+}
+
 TL_API int tl_thresholds_lognormal_device(const tl_domain* d, double sigma, uint64_t seed, uint32_t* t_dev,
                                           size_t n_t, void* stream)
 {

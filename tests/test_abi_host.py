@@ -223,3 +223,16 @@ def test_from_boundary_errors(T):
         with pytest.raises(T.TilingError) as e:
             T.Domain.from_boundary(lat, steps)
         assert e.value.code == code, (steps, e.value)
+
+
+@pytest.mark.parametrize("kind,args", [("aztec", (9,)), ("rect", (8, 5)), ("hex", (4, 3, 5))])
+def test_volume_thresholds_bit_exact(T, kind, args):
+    dom, st, lat = _builtin(T, kind, args)
+    rng = np.random.default_rng(17)
+    q = np.exp(0.8 * rng.standard_normal(st.shape[1:]))
+    q[0, 0] = 1e-70            # extreme weights round to 0 / clamp to 2^32 - 1
+    q[-1, -1] = 1e70
+    assert np.array_equal(dom.volume_thresholds(q), O.volume_thresholds(lat, q))
+    for bad in (-q, q * 0 + 1e80):
+        with pytest.raises(T.TilingError):
+            dom.volume_thresholds(bad)

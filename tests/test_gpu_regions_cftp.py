@@ -128,3 +128,35 @@ def test_cftp_gives_up_at_tmax(T, ctx):
     with pytest.raises(T.TilingError) as e:
         T.cftp(ctx, dom, seed=1, th=T.thresholds(scalar=1 << 31), t0=1, tmax=4)
     assert e.value.code == T.TL_EBUDGET
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_volume_weighted_domino_parity(T, ctx, kernel):
+    # volume weights q = 20 on black vertices (x + y even) and 1/20 on white
+    # ones, and random ones (Sec. 1.1.1), per-site thresholds on both paths
+    n = 70
+    st = O.aztec(n)
+    yy, xx = np.mgrid[0:2 * n + 1, 0:2 * n + 1]
+    for q in (np.where((xx + yy) % 2 == 0, 20.0, 1 / 20.0),
+              np.exp(0.3 * np.random.default_rng(2).standard_normal(xx.shape))):
+        dom = T.Domain.aztec(n)
+        t = dom.volume_thresholds(q)
+        assert np.array_equal(t, O.volume_thresholds(O.DOMINO, q))
+        ch = T.Chain(ctx, dom, seed=13, stream_id=1, th=T.thresholds(site=t))
+        ch.set_plan(kernel)
+        s = st.copy()
+        ring = ch.run_hashed(30)
+        ohash = O.sweeps(O.DOMINO, s, seed=13, stream=1, k=30, t_site=t, want_hashes=True)
+        assert np.array_equal(ring, ohash)
+        assert np.array_equal(ch.read_state(), s)
+
+
+def test_cftp_volume_weighted_matches_oracle(T, ctx):
+    n = 9
+    dom, st0 = T.Domain.aztec(n), O.aztec(n)
+    q = np.exp(0.5 * np.random.default_rng(4).standard_normal(st0.shape[1:]))
+    t = O.volume_thresholds(O.DOMINO, q)
+    top, bot = O.extreme(O.DOMINO, st0, True), O.extreme(O.DOMINO, st0, False)
+    want, T_o = O.cftp(O.DOMINO, top, bot, seed=31, stream=0, t0=4, t_site=t)
+    got, T_g = T.cftp(ctx, dom, seed=31, th=T.thresholds(site=t), t0=4)
+    assert T_g == T_o and np.array_equal(got, want)

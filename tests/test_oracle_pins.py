@@ -727,3 +727,40 @@ def test_coupled_chains_stay_ordered():
             O.sweeps(lat, a, seed=9, sweep0=s, k=1, **kw)
             O.sweeps(lat, b, seed=9, sweep0=s, k=1, **kw)
             assert np.all(O.height(lat, a)[0] >= O.height(lat, b)[0]), (lat, s)
+
+
+# ---------------------------------------------------------------------------
+# Volume weights (Sec. 1.1.1): W(T) = prod_v q_v^h(v)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["aztec3", "rect4x3", "hex222"])
+def test_volume_thresholds_are_stationary(case):
+    lat, st0 = {"aztec3": (O.DOMINO, O.aztec(3)), "rect4x3": (O.DOMINO, O.rect(4, 3)),
+                "hex222": (O.LOZENGE, O.hexagon(2, 2, 2))}[case]
+    rng = np.random.default_rng(5)
+    q = np.exp(0.4 * rng.standard_normal(st0.shape[1:]))
+    t = O.volume_thresholds(lat, q)
+    states, index = enumerate_states(lat, st0)
+    _check_stationary(lat, states, index, [O.volume_weight(lat, s, q) for s in states],
+                      lambda st, y, x: thresh_prob(t[y, x]), 1e-8)
+
+
+def test_volume_weight_one_is_uniform_and_rotation_moves_height_by_four():
+    st = O.aztec(6)
+    t = O.volume_thresholds(O.DOMINO, np.ones(st.shape[1:]))
+    assert np.all(t == 1 << 31)
+    O.sweeps(O.DOMINO, st, seed=8, k=30, t_scalar=1 << 31)
+    # the parity rule: UP raises h(v) by 4 at x + y even and lowers it at odd
+    h0, _ = O.height(O.DOMINO, st)
+    for p in range(2):
+        codes = O.site_states(O.DOMINO, st, p)
+        ys, xs = np.nonzero(codes == 1)          # DOWN sites of this class
+        y, x = ys[0], xs[0]
+        dec = (codes == 2).astype(np.uint8)
+        dec[y, x] = 1
+        nxt = st.copy()
+        O.apply_pass(O.DOMINO, nxt, p, dec)
+        h1, _ = O.height(O.DOMINO, nxt)
+        diff = h1 - h0
+        assert diff[y, x] == (4 if (x + y) % 2 == 0 else -4)
+        diff[y, x] = 0
+        assert not np.any(diff[h0 != O.HEIGHT_NONE])
