@@ -272,6 +272,20 @@ int tl_chain_reset(tl_chain* c, void* stream);
 /* Absolute sweep index of the chain (number of sweeps run so far). */
 uint64_t tl_chain_sweep(const tl_chain* c);
 
+/* Pass order of the chain's sweeps.  TL_ORDER_FIXED (default) visits the
+ * colour classes in their fixed order (dominoes 0, 1; lozenges 0, 1, 2;
+ * six-vertex (0,0), (1,1), (1,0), (0,1)).  TL_ORDER_RANDOM follows
+ * RandomWalk (Sec. 2.2), which picks the colour of every step at random:
+ * slot i of sweep s updates colour floor(P w / 2^32), P the number of
+ * colours and w word 0 of Philox4x32-10(key = seed, counter = (2^32 - 1, s,
+ * 0xFFFF0000 | i, stream_id)), and the site draws of that slot use pass
+ * field i.  Every pass preserves the Gibbs measure, so both orders sample
+ * it.  Chains with the random order cannot join a batch (TL_EUNSUPPORTED
+ * there).  Errors: TL_EINVAL. */
+#define TL_ORDER_FIXED 0
+#define TL_ORDER_RANDOM 1
+int tl_chain_set_order(tl_chain* c, int order);
+
 /* Set the absolute index of the next sweep (0 .. 2^32 - 1).  Random numbers
  * are keyed by this index, so seeking replays or skips randomness; coupling
  * from the past uses it to place runs at negative times.  Sweeps run after a

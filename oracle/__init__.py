@@ -49,13 +49,14 @@ def lib():
             "or_philox4x32_10": (None, [u32p, u32p, u32p]),
             "or_site_u": (c.c_uint32, [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64]),
             "or_splitmix64": (c.c_uint64, [c.c_uint64]),
+            "or_slot_colour": (c.c_int, [c.c_uint64, c.c_uint32, c.c_uint32, c.c_int, c.c_int]),
             "or_state_hash": (c.c_uint64, [u8p, c.c_uint64]),
             "or_domino_aztec_init": (c.c_int, [c.c_int, u8p]),
             "or_domino_rect_init": (c.c_int, [c.c_int, c.c_int, u8p]),
             "or_domino_site_states": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
             "or_domino_apply_pass": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
             "or_domino_sweeps": (c.c_int, [u8p, c.c_int, c.c_int, u32p, c.c_uint32, c.c_uint64,
-                                           c.c_uint32, c.c_uint64, c.c_uint64, u64p]),
+                                           c.c_uint32, c.c_uint64, c.c_uint64, u64p, c.c_int]),
             "or_domino_thresholds": (None, [dp, c.c_int, c.c_int, u32p]),
             "or_domino_weight": (c.c_double, [u8p, c.c_int, c.c_int, dp]),
             "or_domino_check": (c.c_int64, [u8p, c.c_int, c.c_int, u8p]),
@@ -64,7 +65,7 @@ def lib():
             "or_lozenge_site_states": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
             "or_lozenge_apply_pass": (None, [u8p, c.c_int, c.c_int, c.c_int, u8p]),
             "or_lozenge_sweeps": (c.c_int, [u8p, c.c_int, c.c_int, u32p, c.c_uint32, c.c_uint64,
-                                            c.c_uint32, c.c_uint64, c.c_uint64, u64p]),
+                                            c.c_uint32, c.c_uint64, c.c_uint64, u64p, c.c_int]),
             "or_lozenge_thresholds": (c.c_int, [c.c_double, u32p, u32p]),
             "or_lozenge_check": (c.c_int64, [u8p, c.c_int, c.c_int, u8p, u8p]),
             "or_lozenge_height": (c.c_int64, [u8p, c.c_int, c.c_int, i32p]),
@@ -74,7 +75,7 @@ def lib():
             "or_sixv_site_states": (None, [u8p, c.c_int, c.c_int, u8p]),
             "or_sixv_apply_pass": (None, [u8p, c.c_int, c.c_int, u8p]),
             "or_sixv_sweeps": (c.c_int, [u8p, c.c_int, u32p, c.c_uint64, c.c_uint32, c.c_uint64,
-                                         c.c_uint64, u64p]),
+                                         c.c_uint64, u64p, c.c_int]),
             "or_sixv_weight": (c.c_double, [u8p, c.c_int, dp]),
             "or_sixv_thresholds": (c.c_int, [dp, u32p]),
             "or_sixv_height": (c.c_int64, [u8p, c.c_int, i32p]),
@@ -108,6 +109,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 def site_u(seed: int, stream: int, sweep: int, pass_: int, rank: int) -> int:
     """The 32-bit uniform of one site, bit-plane keyed (module docstring of oracle.c)."""
     return int(lib().or_site_u(seed, stream, sweep, pass_, rank))
+
+
+def slot_colour(seed: int, stream: int, sweep: int, slot: int, passes: int) -> int:
+    """Colour visited by pass slot `slot` of sweep `sweep` in random order."""
+    return int(lib().or_slot_colour(seed, stream, sweep, slot, passes))
 
 
 def splitmix64(x: int) -> int:
@@ -191,7 +197,7 @@ def apply_pass(lattice: str, st: np.ndarray, pass_: int, dec: np.ndarray) -> Non
 
 def sweeps(lattice: str, st: np.ndarray, *, seed: int, stream: int = 0, sweep0: int = 0,
            k: int = 1, t_scalar: int | None = None, t_site: np.ndarray | None = None,
-           t16: np.ndarray | None = None, want_hashes: bool = False):
+           t16: np.ndarray | None = None, want_hashes: bool = False, random_order: bool = False):
     """Run k heat-bath sweeps in place (Eq. 1.1 with colour-class clusters).
 
     Domino / lozenge: threshold t_site ([H, W] uint32) or t_scalar.  Six-vertex:
@@ -209,11 +215,12 @@ def sweeps(lattice: str, st: np.ndarray, *, seed: int, stream: int = 0, sweep0: 
             assert ts.shape == (H, W)
         tsc = 0 if t_scalar is None else int(t_scalar)
         fn = L.or_domino_sweeps if lattice == DOMINO else L.or_lozenge_sweeps
-        rc = fn(_p(st), W, H, _p(ts) if ts is not None else None, tsc, seed, stream, sweep0, k, hp)
+        rc = fn(_p(st), W, H, _p(ts) if ts is not None else None, tsc, seed, stream, sweep0, k, hp,
+                int(random_order))
     else:
         t = np.ascontiguousarray(t16, dtype=np.uint32)
         assert t.shape == (16,)
-        rc = L.or_sixv_sweeps(_p(st), W - 2, _p(t), seed, stream, sweep0, k, hp)
+        rc = L.or_sixv_sweeps(_p(st), W - 2, _p(t), seed, stream, sweep0, k, hp, int(random_order))
     if rc != 0:
         raise MemoryError("oracle sweep failed")
     return hashes[:k] if want_hashes else None

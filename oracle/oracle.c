@@ -119,6 +119,23 @@ static uint64_t splitmix64(uint64_t x)
 
 OR_EXPORT uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
 
+/* Random pass order (the RandomWalk of Sec. 2.2 picks the colour of every  */
+/* step at random): slot i of sweep s visits colour floor(P w / 2^32), w =  */
+/* word 0 of Philox4x32-10 with counter (2^32-1, s, 0xFFFF0000 | i, stream) */
+/* (a counter no site draw uses).  The site draws of that slot are keyed    */
+/* by the slot i, so two slots of one sweep on the same colour use fresh    */
+/* numbers.                                                                 */
+OR_EXPORT int or_slot_colour(uint64_t seed, uint32_t stream, uint32_t sweep, int slot, int P)
+{
+    uint32_t ctr[4] = {0xFFFFFFFFu, sweep, 0xFFFF0000u | (uint32_t)slot, stream};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    return (int)(((uint64_t)out[0] * (uint64_t)P) >> 32);
+}
+
+
+
 OR_EXPORT uint64_t or_state_hash(const uint8_t* st, uint64_t nbits)
 {
     uint64_t h = 0;
@@ -230,14 +247,15 @@ OR_EXPORT void or_domino_apply_pass(uint8_t* st, int W, int H, int pass,
 OR_EXPORT int or_domino_sweeps(uint8_t* st, int W, int H,
                                const uint32_t* t_site, uint32_t t_scalar,
                                uint64_t seed, uint32_t stream, uint64_t sweep0,
-                               uint64_t nsweeps, uint64_t* hashes)
+                               uint64_t nsweeps, uint64_t* hashes, int random_order)
 {
     uint64_t Rp = round_up_128((uint64_t)(W + 1) / 2);
     uint8_t* dec = (uint8_t*)calloc((size_t)W * H, 1);
     if (!dec) return -1;
     u_cache cache; cache.valid = 0;
     for (uint64_t s = sweep0; s < sweep0 + nsweeps; ++s) {
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int slot = 0; slot < 2; ++slot) {
+            const int pass = random_order ? or_slot_colour(seed, stream, (uint32_t)s, slot, 2) : slot;
             /* draw the decisions for every rotatable site of the class ... */
             for (int y = 0; y < H; ++y)
                 for (int x = 0; x < W; ++x) {
@@ -247,7 +265,7 @@ OR_EXPORT int or_domino_sweeps(uint8_t* st, int W, int H,
                     if (domino_site_state(st, W, H, x, y) == 0) continue;
                     uint64_t rank = (uint64_t)y * Rp + (uint64_t)(x >> 1);
                     uint32_t u = site_u(&cache, seed, stream, (uint32_t)s,
-                                        (uint32_t)pass, rank);
+                                        (uint32_t)slot, rank);
                     uint32_t t = t_site ? t_site[i] : t_scalar;
                     dec[i] = (u < t) ? 1 : 0;
                 }
@@ -472,14 +490,15 @@ OR_EXPORT void or_lozenge_apply_pass(uint8_t* st, int W, int H, int pass,
 OR_EXPORT int or_lozenge_sweeps(uint8_t* st, int W, int H,
                                 const uint32_t* t_site, uint32_t t_scalar,
                                 uint64_t seed, uint32_t stream, uint64_t sweep0,
-                                uint64_t nsweeps, uint64_t* hashes)
+                                uint64_t nsweeps, uint64_t* hashes, int random_order)
 {
     uint64_t Rp = round_up_128((uint64_t)(W + 2) / 3);
     uint8_t* dec = (uint8_t*)calloc((size_t)W * H, 1);
     if (!dec) return -1;
     u_cache cache; cache.valid = 0;
     for (uint64_t s = sweep0; s < sweep0 + nsweeps; ++s) {
-        for (int pass = 0; pass < 3; ++pass) {
+        for (int slot = 0; slot < 3; ++slot) {
+            const int pass = random_order ? or_slot_colour(seed, stream, (uint32_t)s, slot, 3) : slot;
             for (int y = 0; y < H; ++y)
                 for (int x = 0; x < W; ++x) {
                     size_t i = (size_t)y * W + x;
@@ -488,7 +507,7 @@ OR_EXPORT int or_lozenge_sweeps(uint8_t* st, int W, int H,
                     if (lozenge_site_state(st, W, H, x, y) == 0) continue;
                     uint64_t rank = (uint64_t)y * Rp + (uint64_t)(x / 3);
                     uint32_t u = site_u(&cache, seed, stream, (uint32_t)s,
-                                        (uint32_t)pass, rank);
+                                        (uint32_t)slot, rank);
                     uint32_t t = t_site ? t_site[i] : t_scalar;
                     dec[i] = (u < t) ? 1 : 0;
                 }
@@ -741,7 +760,7 @@ static int sixv_index(const uint8_t* st, int B, int X, int Y)
 
 OR_EXPORT int or_sixv_sweeps(uint8_t* st, int N, const uint32_t t16[16],
                              uint64_t seed, uint32_t stream, uint64_t sweep0,
-                             uint64_t nsweeps, uint64_t* hashes)
+                             uint64_t nsweeps, uint64_t* hashes, int random_order)
 {
     int B = N + 2;
     uint64_t Rp = round_up_128((uint64_t)(B + 1) / 2);
@@ -749,7 +768,8 @@ OR_EXPORT int or_sixv_sweeps(uint8_t* st, int N, const uint32_t t16[16],
     if (!dec) return -1;
     u_cache cache; cache.valid = 0;
     for (uint64_t s = sweep0; s < sweep0 + nsweeps; ++s) {
-        for (int pass = 0; pass < 4; ++pass) {
+        for (int slot = 0; slot < 4; ++slot) {
+            const int pass = random_order ? or_slot_colour(seed, stream, (uint32_t)s, slot, 4) : slot;
             for (int Y = 0; Y < B; ++Y)
                 for (int X = 0; X < B; ++X) {
                     size_t i = (size_t)Y * B + X;
@@ -758,7 +778,7 @@ OR_EXPORT int or_sixv_sweeps(uint8_t* st, int N, const uint32_t t16[16],
                     if (sixv_face_state(st, B, X, Y) == 0) continue;
                     uint64_t rank = (uint64_t)(Y >> 1) * Rp + (uint64_t)(X >> 1);
                     uint32_t u = site_u(&cache, seed, stream, (uint32_t)s,
-                                        (uint32_t)pass, rank);
+                                        (uint32_t)slot, rank);
                     dec[i] = (u < t16[sixv_index(st, B, X, Y)]) ? 1 : 0;
                 }
             or_sixv_apply_pass(st, N, pass, dec);

@@ -99,6 +99,7 @@ _SIG = {
     "tl_chain_reset": (_i, [_vp, _vp]),
     "tl_chain_sweep": (_u64, [_vp]),
     "tl_chain_seek": (_i, [_vp, _u64]),
+    "tl_chain_set_order": (_i, [_vp, _i]),
     "tl_cftp": (_i, [_vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds), _u64, _u64, _vp, ctypes.c_size_t,
                      ctypes.POINTER(_u64), _vp]),
     "tl_chain_launches": (_u64, [_vp]),
@@ -351,6 +352,10 @@ class Chain:
 
     def seek(self, sweep: int):
         _check(_lib.tl_chain_seek(self._h, sweep))
+
+    def set_order(self, random: bool):
+        """Fixed colour order per sweep, or a random colour for every pass slot."""
+        _check(_lib.tl_chain_set_order(self._h, 1 if random else 0))
 
     def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0,
                  threads: int = 0, npre: int = 0):

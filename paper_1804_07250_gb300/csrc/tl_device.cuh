@@ -101,6 +101,16 @@ struct RndPhilox {
         return philox10(grp, sweep, ((uint32_t)k << 16) | pass, rng.stream, rng.k0, rng.k1);
     }
 };
+// Colour of pass slot `slot` of sweep `sweep` when the pass order is random
+// (RandomWalk, Sec. 2.2, picks each step's colour at random): word 0 of the
+// Philox output for counter (2^32-1, sweep, 0xFFFF0000 | slot, stream), a
+// counter no site draw uses, scaled to [0, P).
+TL_DEV uint32_t slot_colour(const DevRng& rng, uint32_t sweep, uint32_t slot, int P)
+{
+    const uint4 o = philox10(0xFFFFFFFFu, sweep, 0xFFFF0000u | slot, rng.stream, rng.k0, rng.k1);
+    return (uint32_t)(((uint64_t)o.x * (uint64_t)P) >> 32);
+}
+
 // The first `npre` planes precomputed (shared memory, plane-major with
 // stride `stride` uint4s), the rest computed on the spot.
 struct RndPre {

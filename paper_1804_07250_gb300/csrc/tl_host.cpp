@@ -914,6 +914,7 @@ struct tl_chain {
     int* status_d = nullptr;
     int threads_req = 0, npre_req = 0;
     bool no_fast = false;
+    int random_order = 0;   // colours of the pass slots drawn per sweep
     unsigned int epoch = 0;
     std::string res_why;
 };
@@ -1153,13 +1154,39 @@ TL_API int tl_chain_get_plan(tl_chain* c, tl_plan* p)
 
 // Sweeps [c->sweep, c->sweep + n) with no density sample inside, one launch
 // per pass over global memory.
+// Philox4x32-10 on the host (Salmon et al., SC'11), for the colour draws of
+// the random pass order: ten rounds of two 32x32 -> 64-bit products by the
+// round multipliers, high halves mixed into the other words and the key.
+static void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = (uint32_t)p1;
+        c[2] = n2;
+        c[3] = (uint32_t)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Colour of pass slot `slot` of sweep `sweep` (same rule as the kernels).
+static uint32_t slot_colour_host(const DevRng& rng, uint32_t sweep, uint32_t slot, int P)
+{
+    uint32_t c[4] = {0xFFFFFFFFu, sweep, 0xFFFF0000u | slot, rng.stream};
+    philox_host(c, rng.k0, rng.k1);
+    return (uint32_t)(((uint64_t)c[0] * (uint64_t)P) >> 32);
+}
+
 static int run_segment(tl_chain* c, uint64_t n, void* stream)
 {
     const Geom& g = c->g;
     for (uint64_t s = 0; s < n; ++s) {
         const uint32_t sw = (uint32_t)(c->sweep + s);
         for (int p = 0; p < g.passes; ++p) {
-            const int e = launch_pass_global(g, c->rows, (uint32_t)p, sw, c->rng, c->th, c->grange, stream);
+            const uint32_t colour = c->random_order ? slot_colour_host(c->rng, sw, (uint32_t)p, g.passes) : (uint32_t)p;
+            const int e = launch_pass_global(g, c->rows, colour, (uint32_t)p, sw, c->rng, c->th, c->grange, stream);
             if (e) return fail(TL_ECUDA, "pass kernel: %s", cudaGetErrorString((cudaError_t)e));
         }
         c->launches += (uint64_t)g.passes;
@@ -1351,7 +1378,7 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
         }
         const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
                                       c->grange, ++c->epoch, ring ? ring + done : nullptr,
-                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, stream);
+                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, c->random_order, stream);
         if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
         if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
         c->sweep += n;
@@ -1507,6 +1534,13 @@ TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
     c->launches += 1;
     CUDA_TRY(cudaMemcpyAsync(out, c->hash, 8, cudaMemcpyDeviceToHost, SS(stream)));
     CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    return TL_OK;
+}
+
+TL_API int tl_chain_set_order(tl_chain* c, int order)
+{
+    if (!c || (order != TL_ORDER_FIXED && order != TL_ORDER_RANDOM)) return fail(TL_EINVAL, "tl_chain_set_order: bad argument");
+    c->random_order = order == TL_ORDER_RANDOM;
     return TL_OK;
 }
 
@@ -1834,6 +1868,7 @@ static int batch_attach(tl_batch* b, tl_chain* c)
 {
     if (!c || c->ctx->device != b->ctx->device) return fail(TL_EINVAL, "batch: chain on another device");
     if (c->density_on) return fail(TL_EINVAL, "batch: chain samples densities");
+    if (c->random_order) return fail(TL_EUNSUPPORTED, "batch: chain uses the random pass order");
     for (auto* x : b->chains)
         if (x == c) return fail(TL_EINVAL, "batch: chain already in the batch");
     uint32_t* a = nullptr;
@@ -1906,6 +1941,7 @@ static int batch_upload_sweeps(tl_batch* b, uint64_t k, void* stream)
     CUDA_TRY(cudaStreamSynchronize(SS(stream)));
     for (size_t i = 0; i < b->chains.size(); ++i) {
         if (b->chains[i]->sweep + k > 0xFFFFFFFFull) return fail(TL_EINVAL, "batch: sweep index beyond 2^32");
+        if (b->chains[i]->random_order) return fail(TL_EUNSUPPORTED, "batch: chain uses the random pass order");
         b->h_sweep[i] = (uint32_t)b->chains[i]->sweep;
     }
     CUDA_TRY(cudaMemcpyAsync(b->d_sweep, b->h_sweep, 4 * b->chains.size(), cudaMemcpyHostToDevice, SS(stream)));

@@ -63,9 +63,10 @@ struct HeightPlan {
 // ---- kernel launchers (tl_kernels.cu); all return cudaError_t as int ----
 int launch_pack(const Geom& g, const uint8_t* canon_dev, uint32_t* rows, void* stream);
 int launch_unpack(const Geom& g, const uint32_t* rows, uint8_t* canon_dev, void* stream);
-int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t sweep,
-                       const DevRng& rng, const ThrView& th, const int2* grange,
-                       void* stream);
+// `pass`: the colour class updated; `slot`: the pass slot that keys the
+// random numbers (equal unless the pass order is random).
+int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t slot, uint32_t sweep,
+                       const DevRng& rng, const ThrView& th, const int2* grange, void* stream);
 int launch_hash(const Geom& g, const uint32_t* rows, unsigned long long* out, void* stream);
 int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* counts, void* stream);
 int launch_density_read(const uint32_t* counts, uint64_t n, uint64_t samples, double* out,
@@ -115,7 +116,7 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, void* stream);
+                    uint32_t stride, int random_order, void* stream);
 
 // ---- batched chains (tl_batch.cu) ----
 struct BatchChain {

@@ -28,7 +28,7 @@ namespace tl {
 // ---------------------------------------------------------------------------
 template <int LAT, int TK>
 __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__ rows0, Geom g,
-                                                          uint32_t pass, uint32_t sweep,
+                                                          uint32_t pass, uint32_t slot, uint32_t sweep,
                                                           DevRng rng, ThrView th,
                                                           const int2* __restrict__ grange)
 {
@@ -50,13 +50,13 @@ __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__
     if (m < gr.x || m >= gr.y) return;
     const uint32_t grp = (uint32_t)(rr * g.Kg + m);
     uint32_t* row = rows0 + (int64_t)y * g.row_words;
-    const RndPhilox rnd{grp, sweep, pass, rng};
+    const RndPhilox rnd{grp, sweep, slot, rng};
     group_update<LAT, TK>(row, g.row_words, g, y, m, pass, rnd, th);
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t sweep,
+int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t slot, uint32_t sweep,
                        const DevRng& rng, const ThrView& th, const int2* grange, void* stream)
 {
     const int nrow = (g.lattice == LAT_SIXV) ? ((g.H + 1) >> 1) : g.H;
@@ -65,16 +65,16 @@ int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t sw
     uint32_t* rows0 = rows + g.row_words;
     if (g.lattice == LAT_DOMINO) {
         if (th.kind == THR_SITE)
-            pass_global_kernel<LAT_DOMINO, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, sweep, rng, th, grange);
+            pass_global_kernel<LAT_DOMINO, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
         else
-            pass_global_kernel<LAT_DOMINO, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, sweep, rng, th, grange);
+            pass_global_kernel<LAT_DOMINO, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
     } else if (g.lattice == LAT_LOZENGE) {
         if (th.kind == THR_SITE)
-            pass_global_kernel<LAT_LOZENGE, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, sweep, rng, th, grange);
+            pass_global_kernel<LAT_LOZENGE, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
         else
-            pass_global_kernel<LAT_LOZENGE, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, sweep, rng, th, grange);
+            pass_global_kernel<LAT_LOZENGE, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
     } else {
-        pass_global_kernel<LAT_SIXV, THR_TABLE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, sweep, rng, th, grange);
+        pass_global_kernel<LAT_SIXV, THR_TABLE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
     }
     return (int)cudaGetLastError();
 }

@@ -36,6 +36,7 @@ struct ResParams {
     Geom g;
     const int* stripe_lo;
     int halo, npre;
+    int random_order;           // colours of the pass slots drawn per sweep
     int cap_items;              // item-table capacity per CTA
     int cap_cycle;              // random-plane buffer capacity (groups per cycle)
     uint32_t sweep0, nsweeps;
@@ -229,13 +230,16 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
     while (done < total) {
         const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
-        // pass table of this cycle: item range, random-plane slot, sweep, pass
+        // pass table of this cycle: item range, random-plane offset, pass slot
+        // | colour << 8, sweep.  The slot keys the random numbers, the colour
+        // (the slot itself unless the order is random) selects the sites.
         if (tid == 0) {
             uint32_t sweep = cyc_sweep, pass = cyc_pass;
             int base = 0;
             for (int i = 1; i <= hc; ++i) {
-                const PassRange pr = pass_range<LAT>(g, i, pass, slo, shi, bot, top, off, nloc);
-                s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)pass);
+                const uint32_t colour = P.random_order ? slot_colour(P.rng, sweep, pass, passes) : pass;
+                const PassRange pr = pass_range<LAT>(g, i, colour, slo, shi, bot, top, off, nloc);
+                s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)(pass | (colour << 8)));
                 s_psweep[i - 1] = sweep;
                 base += pr.e - pr.s;
                 if (++pass == (uint32_t)passes) {
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         auto gen = [&](int i) {
             const int4 e = s_ptab[i];
             if (e.y <= 0) return;
-            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
+            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w & 255u;   // slot
             const uint32_t d = (uint32_t)e.y, mg = 0xFFFFFFFFu / d + 1u;
             const int n = P.npre * e.y;
             for (int b0 = rtid; b0 < n; b0 += 2 * HALF) {
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         __syncthreads();
         for (int i = 0; i < hc; ++i) {
             const int4 e = s_ptab[i];
-            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w;
+            const uint32_t sweep = s_psweep[i], slot = (uint32_t)e.w & 255u, pass = (uint32_t)e.w >> 8;
             if (FAST && upd_role) {
                 // read and decide every group of the pass, then store: groups
                 // read their neighbours' boundary words
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     const uint32_t item = items[e.x + it];
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                     const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                    const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, pass, P.rng}};
+                    const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, slot, P.rng}};
                     group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th,
                                           LAT == LAT_SIXV ? s_ttab : nullptr, ctab);
                 }
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 gen(i + 1);
             }
             __syncthreads();
-            if (pass == (uint32_t)(passes - 1)) {
+            if (slot == (uint32_t)(passes - 1)) {
                 // end of a sweep: the owned rows are exact (i < halo)
                 const uint64_t ndone = (uint64_t)sweep + 1;
                 const bool sample = P.counts && P.stride && ndone >= P.burn &&
@@ -470,7 +474,7 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, void* stream)
+                    uint32_t stride, int random_order, void* stream)
 {
     ResParams P;
     P.rows0 = rows + g.row_words;
@@ -478,6 +482,7 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     P.stripe_lo = plan.stripe_lo;
     P.halo = plan.halo;
     P.npre = plan.npre;
+    P.random_order = random_order;
     P.cap_items = plan.cap_items;
     P.cap_cycle = plan.cap_cycle;
     P.sweep0 = sweep0;

@@ -160,3 +160,36 @@ def test_cftp_volume_weighted_matches_oracle(T, ctx):
     want, T_o = O.cftp(O.DOMINO, top, bot, seed=31, stream=0, t0=4, t_site=t)
     got, T_g = T.cftp(ctx, dom, seed=31, th=T.thresholds(site=t), t0=4)
     assert T_g == T_o and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kernel,halo", [(1, 0), (2, 0), (2, 3), (2, 5)])
+@pytest.mark.parametrize("kind", ["aztec", "aztec_t", "hex", "dwbc"])
+def test_random_order_parity(T, ctx, kind, kernel, halo):
+    # random colour per pass slot (RandomWalk, Sec. 2.2) on both paths
+    if kind.startswith("aztec"):
+        dom, st, lat = T.Domain.aztec(90), O.aztec(90), O.DOMINO
+        t = (1 << 31) if kind == "aztec" else 0x5A000000
+        th, okw = T.thresholds(scalar=t), dict(t_scalar=t)
+    elif kind == "hex":
+        dom, st, lat = T.Domain.hexagon(60, 70, 50), O.hexagon(60, 70, 50), O.LOZENGE
+        ta, _ = O.lozenge_thresholds(1.1)
+        th, okw = T.thresholds(scalar=ta), dict(t_scalar=ta)
+    else:
+        dom, st, lat = T.Domain.dwbc(150), O.dwbc(150), O.SIXV
+        t16 = O.sixv_thresholds(SQ2)
+        th, okw = T.thresholds(table16=t16), dict(t16=t16)
+    ch = T.Chain(ctx, dom, seed=101, stream_id=6, th=th)
+    ch.set_plan(kernel, 0, halo)
+    ch.set_order(True)
+    ring = ch.run_hashed(24)
+    ohash = O.sweeps(lat, st, seed=101, stream=6, k=24, random_order=True, want_hashes=True, **okw)
+    assert np.array_equal(ring, ohash)
+    assert np.array_equal(ch.read_state(), st)
+
+
+def test_random_order_chain_cannot_join_a_batch(T, ctx):
+    ch = T.Chain(ctx, T.Domain.aztec(20), seed=1, th=T.thresholds(scalar=1 << 31))
+    ch.set_order(True)
+    with pytest.raises(T.TilingError) as e:
+        T.Batch(ctx, [ch])
+    assert e.value.code == T.TL_EUNSUPPORTED

@@ -764,3 +764,55 @@ def test_volume_weight_one_is_uniform_and_rotation_moves_height_by_four():
         assert diff[y, x] == (4 if (x + y) % 2 == 0 else -4)
         diff[y, x] = 0
         assert not np.any(diff[h0 != O.HEIGHT_NONE])
+
+
+# ---------------------------------------------------------------------------
+# Random pass order (the RandomWalk of Sec. 2.2 picks each step's colour at
+# random)
+# ---------------------------------------------------------------------------
+def test_slot_colours_uniform_and_from_philox():
+    from scipy.stats import chisquare
+    for P in (2, 3, 4):
+        cols = np.array([O.slot_colour(99, 5, s, i, P) for s in range(3000) for i in range(P)])
+        assert cols.min() >= 0 and cols.max() < P
+        assert chisquare(np.bincount(cols, minlength=P)).pvalue > 1e-4
+        # pairs of consecutive slots are independent
+        pairs = cols[:-1] * P + cols[1:]
+        assert chisquare(np.bincount(pairs, minlength=P * P)).pvalue > 1e-4
+    # the draw is word 0 of the Random123 Philox output for its counter, scaled
+    out = O.philox4x32_10([0xFFFFFFFF, 17, 0xFFFF0002, 5], [99, 0])
+    assert O.slot_colour(99, 5, 17, 2, 3) == (int(out[0]) * 3) >> 32
+
+
+@pytest.mark.parametrize("case", ["aztec3", "hex222", "dwbc4"])
+def test_random_order_chain_chi_square(case):
+    if case == "aztec3":
+        lat, st0, kw = O.DOMINO, O.aztec(3), dict(t_scalar=1 << 31)
+        states, index = enumerate_states(lat, st0)
+        pi = np.ones(len(states))
+    elif case == "hex222":
+        lat, st0 = O.LOZENGE, O.hexagon(2, 2, 2)
+        ta, _ = O.lozenge_thresholds(1.5)
+        kw = dict(t_scalar=ta)
+        h0, _ = O.height(O.LOZENGE, st0)
+        states, index = enumerate_states(lat, st0)
+        pi = np.array([1.5 ** _volume(s, h0) for s in states])
+    else:
+        lat, st0 = O.SIXV, O.dwbc(4)
+        w6 = [1, 1, 1, 1, math.sqrt(2), math.sqrt(2)]
+        kw = dict(t16=O.sixv_thresholds(w6))
+        states, index = enumerate_states(lat, st0)
+        pi = np.array([O.sixv_weight(s, w6) for s in states])
+    pi = pi / pi.sum()
+    counts = np.zeros(len(states))
+    st = st0.copy()
+    O.sweeps(lat, st, seed=7, stream=2, sweep0=0, k=30, random_order=True, **kw)
+    for i in range(3000):
+        O.sweeps(lat, st, seed=7, stream=2, sweep0=30 + 6 * i, k=6, random_order=True, **kw)
+        counts[index[st.tobytes()]] += 1
+    assert _chi2_pvalue(counts, pi) > 1e-4
+    # and the order really differs from the fixed one
+    a, b = st0.copy(), st0.copy()
+    O.sweeps(lat, a, seed=7, k=5, **kw)
+    O.sweeps(lat, b, seed=7, k=5, random_order=True, **kw)
+    assert not np.array_equal(a, b)
