@@ -530,6 +530,80 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Exact samplers: domino shuffling of the Aztec diamond of order 2048, and
+# coupling from the past on the Aztec diamond of order 128 (uniform).
+# ---------------------------------------------------------------------------
+EXACT = {"shuffle2048": ("aztec_diamond_n2048_domino_shuffling", 2048),
+         "cftp_aztec128": ("aztec_diamond_n128_coupling_from_the_past", 128)}
+
+
+def run_exact(args):
+    import numpy as np
+    import torch
+    import paper_1804_07250_gb300 as T
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = T.Context(local)
+    name, n = EXACT[args.workload]
+    stream = torch.cuda.Stream()
+    shuffle = args.workload.startswith("shuffle")
+    dom = None if shuffle else T.Domain.aztec(n)
+    th = T.thresholds(scalar=UNIFORM_T)
+    out_dev = torch.empty((2, 2 * n + 1, 2 * n + 1), dtype=torch.uint8, device="cuda")
+
+    def one(seed):
+        if shuffle:
+            T.aztec_shuffle(ctx, n, seed=seed, stream_id=rank, out=out_dev, stream=stream)
+            return 0
+        _, t_used = T.cftp(ctx, dom, seed=seed, stream_id=rank, th=th, t0=64, out=out_dev, stream=stream)
+        return t_used
+
+    for w in range(args.warmup):
+        one(10_000 + w)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    used = [one(s) for s in range(args.steps)]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clocks = sampler.stop()
+    value = world * args.steps / dt
+    # work: shuffling touches sum_k (2k)^2 cells; CFTP runs 2 chains over
+    # 64 + 128 + ... + T sweeps of n^2 + (n-1)^2 sites
+    sites = n * n + (n - 1) ** 2
+    if shuffle:
+        cells = sum((2 * k) ** 2 for k in range(1, n + 1))
+        extra = {"cell_updates_per_s": cells * args.steps / dt}
+    else:
+        sweeps = [2 * (2 * t - 64) for t in used]
+        extra = {"flip_attempts_per_s": sites * sum(sweeps) / dt, "T_used": used}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        if shuffle:
+            m = 96
+            t1 = time.perf_counter()
+            O.aztec_shuffle(m, 1)
+            d1 = time.perf_counter() - t1
+            cells_m = sum((2 * k) ** 2 for k in range(1, m + 1))
+            cpu = {"value": cells_m / d1, "unit": "cell updates/s", "cores": 1, "kind": "oracle",
+                   "sample": "one oracle shuffle of order %d (%.1f s)" % (m, d1)}
+        else:
+            r, d1, _ = oracle_rate(WORKLOADS["aztec2048"] | {"size": (n,)}, 400, sites)
+            cpu = {"value": r, "unit": "flip attempts/s", "cores": 1, "kind": "oracle",
+                   "sample": "400 oracle sweeps of the order-%d diamond (%.1f s)" % (n, d1)}
+    if rank == 0:
+        line = {"metric": "exact samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "config": {"workload": name, "n": n, "seeds": "0..steps-1",
+                                                "l2": "state fits in L2; no flush (each step allocates its buffers)"},
+                **extra, "clocks": clocks, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,7 +615,7 @@ def main():
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=[*WORKLOADS, "batch", "serve"], default="aztec2048")
+    ap.add_argument("--workload", choices=[*WORKLOADS, *EXACT, "batch", "serve"], default="aztec2048")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=80.0)
@@ -554,6 +628,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         run_serve(args)
+        return
+    if args.workload in EXACT and args.impl == "ours":
+        run_exact(args)
         return
     if args.impl == "reference":
         if args.workload not in WORKLOADS:

@@ -292,6 +292,19 @@ int tl_chain_set_order(tl_chain* c, int order);
  * seek must stay below 2^32.  Errors: TL_EINVAL. */
 int tl_chain_seek(tl_chain* c, uint64_t sweep);
 
+/* Exact uniform random tiling of the Aztec diamond of order n (1 <= n <=
+ * 32767) by domino shuffling (the shuffling algorithms of Sec. 3; Elkies,
+ * Kuperberg, Larsen and Propp), independent of the Markov chain: n growth
+ * steps of destruction, sliding and creation, all on the device.  The draw
+ * of the 2x2 block created with lower-left cell (x, y) (cells centred on the
+ * diamond, x, y in [-n, n)) at order K is word 0 of Philox4x32-10(key =
+ * seed, counter = ((y+n) << 16 | (x+n), K, 0xFFFE0000, stream_id)): two
+ * horizontal dominoes if it is below 2^31, else two vertical ones.  Writes
+ * the canonical state of tl_domain_aztec(n) to `canon` (host or device, cap
+ * >= 2 (2n+1)^2).  Synchronous.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_id, uint8_t* canon, size_t cap,
+                     void* stream);
+
 /* Exact sample by coupling from the past (Sec. 1.1.4; Propp and Wilson).
  * Two chains start from TL_EXTREME_TOP and TL_EXTREME_BOTTOM with the same
  * seed and stream id and run the sweeps with absolute indices 2^32 - T ..

@@ -561,3 +561,86 @@ def cftp(lattice: str, st_top: np.ndarray, st_bot: np.ndarray, *, seed: int, str
         if 2 * T > tmax:
             raise RuntimeError("no coalescence within %d sweeps" % T)
         T *= 2
+
+
+# --------------------------------------------------------------------------
+# Domino shuffling: exact uniform sampling of the Aztec diamond (Sec. 3,
+# shuffling algorithms; Elkies, Kuperberg, Larsen and Propp)
+# --------------------------------------------------------------------------
+def shuffle_bit(seed: int, stream: int, order: int, x: int, y: int, n: int) -> int:
+    """Orientation draw of the 2x2 block created with lower-left cell (x, y)
+    (cell coordinates centred on the diamond) when growing to order `order`
+    in a run of final order n: 1 = two horizontal dominoes.  Word 0 of
+    Philox4x32-10 with key = seed and counter ((y+n) << 16 | (x+n), order,
+    0xFFFE0000, stream), compared with 2^31."""
+    w = philox4x32_10([((y + n) << 16) | (x + n), order, 0xFFFE0000, stream],
+                      [seed & 0xFFFFFFFF, seed >> 32])
+    return 1 if int(w[0]) < (1 << 31) else 0
+
+
+def aztec_shuffle(n: int, seed: int, stream: int = 0) -> np.ndarray:
+    """Uniform random tiling of the Aztec diamond of order n by domino
+    shuffling, in the canonical layout of aztec(n).
+
+    Cells are unit squares with lower-left corner (x, y), the diamond of order
+    k being |x + 1/2| + |y + 1/2| <= k.  In order k a horizontal domino with
+    left cell (x, y) goes north if x + y + k is even and south otherwise; a
+    vertical one with bottom cell (x, y) goes east if x + y + k is even and
+    west otherwise (the top row's domino goes north, the left column's
+    west).  One step k -> k+1: delete the bad blocks (a north-going domino
+    directly below a south-going one, an east-going one directly left of a
+    west-going one: they would pass through each other), move every other
+    domino one cell in its direction, and fill the cells of order k+1 left
+    empty, which form disjoint 2x2 blocks, block by block, taking the lowest
+    then leftmost empty cell as a block's lower-left corner: two horizontal
+    dominoes if the block's draw says so, else two vertical ones."""
+    doms = {}                      # (x, y) of the left / bottom cell -> 0 horizontal, 1 vertical
+    for k in range(n):
+        def goes(x, y, o):
+            even = (x + y + k) % 2 == 0
+            if o == 0:
+                return (0, 1) if even else (0, -1)
+            return (1, 0) if even else (-1, 0)
+        bad = set()
+        for (x, y), o in doms.items():
+            if o == 0 and (x + y + k) % 2 == 0 and doms.get((x, y + 1)) == 0:
+                bad.update(((x, y), (x, y + 1)))
+            if o == 1 and (x + y + k) % 2 == 0 and doms.get((x + 1, y)) == 1:
+                bad.update(((x, y), (x + 1, y)))
+        moved = {}
+        for (x, y), o in doms.items():
+            if (x, y) in bad:
+                continue
+            dx, dy = goes(x, y, o)
+            moved[(x + dx, y + dy)] = o
+        K = k + 1
+        covered = set()
+        for (x, y), o in moved.items():
+            for c in (((x, y), (x + 1, y)) if o == 0 else ((x, y), (x, y + 1))):
+                assert c not in covered
+                covered.add(c)
+        empty = sorted(((x, y) for y in range(-K, K) for x in range(-K, K)
+                        if abs(x + 0.5) + abs(y + 0.5) <= K and (x, y) not in covered),
+                       key=lambda c: (c[1], c[0]))
+        filled = set()
+        for (x, y) in empty:
+            if (x, y) in filled:
+                continue
+            block = ((x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1))
+            assert all(c not in covered and c not in filled for c in block)
+            filled.update(block)
+            if shuffle_bit(seed, stream, K, x, y, n):
+                moved[(x, y)] = 0
+                moved[(x, y + 1)] = 0
+            else:
+                moved[(x, y)] = 1
+                moved[(x + 1, y)] = 1
+        doms = moved
+    W = 2 * n + 1
+    st = np.zeros((2, W, W), dtype=np.uint8)
+    for (x, y), o in doms.items():
+        if o == 0:        # horizontal: crosses the vertical edge between its cells
+            st[1, y + n, x + 1 + n] = 1
+        else:             # vertical: crosses the horizontal edge between its cells
+            st[0, y + 1 + n, x + n] = 1
+    return st

@@ -100,6 +100,7 @@ _SIG = {
     "tl_chain_sweep": (_u64, [_vp]),
     "tl_chain_seek": (_i, [_vp, _u64]),
     "tl_chain_set_order": (_i, [_vp, _i]),
+    "tl_aztec_shuffle": (_i, [_vp, _i, _u64, _u32, _vp, ctypes.c_size_t, _vp]),
     "tl_cftp": (_i, [_vp, _vp, _u64, _u32, ctypes.POINTER(Thresholds), _u64, _u64, _vp, ctypes.c_size_t,
                      ctypes.POINTER(_u64), _vp]),
     "tl_chain_launches": (_u64, [_vp]),
@@ -320,6 +321,15 @@ def cftp(ctx, domain, *, seed: int, stream_id: int = 0, th, t0: int = 64, tmax: 
     _check(_lib.tl_cftp(ctx._h, domain._h, seed, stream_id, ctypes.byref(th), t0, tmax, p, n, ctypes.byref(t),
                         _stream(stream)))
     return out, int(t.value)
+
+
+def aztec_shuffle(ctx, n: int, *, seed: int, stream_id: int = 0, out=None, stream=None):
+    """Exact uniform tiling of the Aztec diamond of order n by domino shuffling."""
+    if out is None:
+        out = np.zeros((2, 2 * n + 1, 2 * n + 1), dtype=np.uint8)
+    p, size = _ptr(out)
+    _check(_lib.tl_aztec_shuffle(ctx._h, n, seed, stream_id, p, size, _stream(stream)))
+    return out
 
 
 class Chain:

@@ -1537,6 +1537,41 @@ TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
     return TL_OK;
 }
 
+TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_id, uint8_t* canon, size_t cap,
+                            void* stream)
+{
+    if (!ctx || !canon || n < 1 || n > 32767) return fail(TL_EINVAL, "tl_aztec_shuffle: bad argument");
+    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W, ncell = (size_t)4 * n * n;
+    if (cap < ncanon) return fail(TL_EINVAL, "tl_aztec_shuffle: cap %zu < %zu", cap, ncanon);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    uint8_t *A = nullptr, *B = nullptr, *F = nullptr, *out = nullptr;
+    int* status = nullptr;
+    const bool dev = is_device_ptr(canon);
+    int rc;
+    if ((rc = dev_alloc(&A, ncell, "shuffle cells")) || (rc = dev_alloc(&B, ncell, "shuffle cells")) ||
+        (rc = dev_alloc(&F, ncell, "shuffle marks")) || (rc = dev_alloc(&status, 1, "status")) ||
+        (!dev && (rc = dev_alloc(&out, ncanon, "shuffle output")))) {
+        cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(status); cudaFree(out);
+        return rc;
+    }
+    uint8_t* dst = dev ? canon : out;
+    DevRng rng{(uint32_t)seed, (uint32_t)(seed >> 32), stream_id};
+    uint64_t launches = 0;
+    cudaError_t e = cudaMemsetAsync(A, 0, ncell, SS(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(B, 0, ncell, SS(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), SS(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, ncanon, SS(stream));
+    if (e == cudaSuccess) e = (cudaError_t)launch_shuffle(n, A, B, F, rng, status, dst, &launches, stream);
+    int hstatus = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, SS(stream));
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(canon, out, ncanon, cudaMemcpyDeviceToHost, SS(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(SS(stream));
+    cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(status); cudaFree(out);
+    if (e != cudaSuccess) return fail(TL_ECUDA, "tl_aztec_shuffle: %s", cudaGetErrorString(e));
+    if (hstatus) return fail(TL_ECUDA, "tl_aztec_shuffle: a created block was not a 2x2 hole");
+    return TL_OK;
+}
+
 TL_API int tl_chain_set_order(tl_chain* c, int order)
 {
     if (!c || (order != TL_ORDER_FIXED && order != TL_ORDER_RANDOM)) return fail(TL_EINVAL, "tl_chain_set_order: bad argument");

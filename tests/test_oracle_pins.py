@@ -816,3 +816,24 @@ def test_random_order_chain_chi_square(case):
     O.sweeps(lat, a, seed=7, k=5, **kw)
     O.sweeps(lat, b, seed=7, k=5, random_order=True, **kw)
     assert not np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# Domino shuffling (Sec. 3): exact uniform tilings of the Aztec diamond
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 5, 13, 30])
+def test_shuffling_gives_tilings_of_the_diamond(n):
+    for seed in range(3):
+        st = O.aztec_shuffle(n, seed, stream=seed)
+        assert O.domino_check(st, _aztec_faces(n)) == 0
+        assert O.height(O.DOMINO, st)[1] == 0
+
+
+def test_shuffling_is_uniform():
+    # every one of the 2^(n(n+1)/2) = 64 tilings of order 3 equally likely
+    states, index = enumerate_states(O.DOMINO, O.aztec(3))
+    assert len(states) == 64
+    counts = np.zeros(64)
+    for seed in range(6400):
+        counts[index[O.aztec_shuffle(3, seed).tobytes()]] += 1
+    assert _chi2_pvalue(counts, np.full(64, 1 / 64)) > 1e-4
