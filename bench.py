@@ -258,7 +258,9 @@ def run_ours(args):
         thr_desc = {"w6": list(wl["w6"]), "t16": [int(v) for v in t16]}
     info = dom.info
     stream = torch.cuda.Stream()
-    chain = T.Chain(ctx, dom, seed=wl["seed"], stream_id=0, th=th)
+    from paper_1804_07250_gb300 import replicas
+    # every rank samples its own replica: same workload, its own stream id
+    chain = T.Chain(ctx, dom, seed=wl["seed"], stream_id=replicas.replica_stream_id(0, rank, world), th=th)
     if args.kernel or args.spl or args.halo or args.threads:
         chain.set_plan(args.kernel, args.spl, args.halo, args.threads)
     hshape = dom.height_shape
@@ -312,10 +314,7 @@ def run_ours(args):
     launches = chain.launches - launches0
     got_hash = int(hash_dev.cpu().numpy().view(np.uint64)[0])
     assert got_hash == ref_hash, "steps are not deterministic"
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms, dist, device="cuda")   # the slowest rank's time
     attempts_step = info.sites * SWEEPS
     value = world * attempts_step * args.steps / (total_ms / 1e3)
 

@@ -1,0 +1,81 @@
+"""Multi-process replicas on CPU (gloo, world size 2): job sharding, the
+slowest-rank timing and the gathering of per-job results, as bench.py and the
+serving loop use them with one process per GPU."""
+from __future__ import annotations
+
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    import json
+
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle as O
+        from paper_1804_07250_gb300 import replicas as R
+
+        jobs = list(range(11))
+        mine = R.shard(jobs, rank, world)
+        # each job: a short oracle chain keyed by its own stream id
+        results = {}
+        for j in mine:
+            st = O.aztec(4)
+            O.sweeps(O.DOMINO, st, seed=3, stream=R.replica_stream_id(j, 0, 1), k=5, t_scalar=1 << 31)
+            results[j] = O.state_hash(st)
+        slowest = R.max_over_ranks(10.0 + rank, dist)
+        gathered = R.gather_results(results, dist)
+        with open(os.path.join(out_dir, "r%d.json" % rank), "w") as f:
+            json.dump({"mine": mine, "slowest": slowest,
+                       "gathered": [{str(k): int(v) for k, v in g.items()} for g in gathered],
+                       "sid": [R.replica_stream_id(7, r, world) for r in range(world)]}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_replicas(tmp_path):
+    import json
+
+    import torch.multiprocessing as mp
+
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    out = [json.load(open(tmp_path / ("r%d.json" % r))) for r in range(world)]
+    # every job on exactly one rank
+    assert sorted(out[0]["mine"] + out[1]["mine"]) == list(range(11))
+    assert not set(out[0]["mine"]) & set(out[1]["mine"])
+    # the job time is the slowest rank's, seen by every rank
+    assert out[0]["slowest"] == out[1]["slowest"] == 11.0
+    # every rank sees all results; a job's result depends on the job only
+    import oracle as O
+    for o in out:
+        merged = {}
+        for g in o["gathered"]:
+            merged.update(g)
+        assert sorted(int(k) for k in merged) == list(range(11))
+        st = O.aztec(4)
+        O.sweeps(O.DOMINO, st, seed=3, stream=4, k=5, t_scalar=1 << 31)
+        assert merged["4"] == O.state_hash(st)
+    assert len(set(out[0]["sid"])) == world
+
+
+def test_single_process_fallbacks():
+    from paper_1804_07250_gb300 import replicas as R
+    assert R.shard([1, 2, 3], 0, 1) == [1, 2, 3]
+    assert R.max_over_ranks(2.5) == 2.5
+    assert R.gather_results({"a": 1}) == [{"a": 1}]
+    assert R.replica_stream_id(5, 0, 1) == 5
+    with pytest.raises(ValueError):
+        R.shard([1], 2, 2)
