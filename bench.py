@@ -240,7 +240,7 @@ def run_ours(args):
     import paper_1804_07250_gb300 as T
 
     wl = WORKLOADS[args.workload]
-    SWEEPS = wl["sweeps"]
+    SWEEPS = args.sweeps or wl["sweeps"]
     ctx = T.Context(local)
     if wl["kind"] == "aztec":
         dom = T.Domain.aztec(*wl["size"])
@@ -614,6 +614,8 @@ def main():
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="sweeps per step instead of the workload's (short runs for profiling only)")
     ap.add_argument("--workload", choices=[*WORKLOADS, *EXACT, "batch", "serve"], default="aztec2048")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
