@@ -915,6 +915,8 @@ struct tl_chain {
     int threads_req = 0, npre_req = 0;
     bool no_fast = false;
     int random_order = 0;   // colours of the pass slots drawn per sweep
+    uint8_t* colours = nullptr;   // device colours of one resident launch's slots
+    size_t colours_cap = 0;
     unsigned int epoch = 0;
     std::string res_why;
 };
@@ -929,6 +931,7 @@ static void chain_free(tl_chain* c)
     cudaFree(c->tplanes);
     cudaFree(c->hash);
     cudaFree(c->counts);
+    cudaFree(c->colours);
     cudaFree(c->hseg);
     cudaFree(c->hbase);
     cudaFree(c->hscratch);
@@ -1376,9 +1379,23 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
             const size_t nx = (size_t)c->res.ctas * 4 * c->res.halo * c->g.row_words;
             CUDA_TRY(cudaMemsetAsync(c->xbuf_d, 0, nx * sizeof(unsigned long long), SS(stream)));
         }
+        if (c->random_order) {
+            const size_t need = (size_t)n * c->g.passes;
+            if (need > c->colours_cap) {
+                CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+                cudaFree(c->colours);
+                c->colours = nullptr;
+                c->colours_cap = 0;
+                TL_TRY(dev_alloc(&c->colours, need, "pass colours"));
+                c->colours_cap = need;
+            }
+            const int ec = launch_slot_colours(c->colours, (uint32_t)c->sweep, (uint32_t)n, c->g.passes, c->rng, stream);
+            if (ec) return fail(TL_ECUDA, "colour kernel: %s", cudaGetErrorString((cudaError_t)ec));
+            c->launches += 1;
+        }
         const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
                                       c->grange, ++c->epoch, ring ? ring + done : nullptr,
-                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, c->random_order, stream);
+                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
         if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
         if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
         c->sweep += n;

@@ -121,7 +121,9 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, int random_order, void* stream);
+                    uint32_t stride, const uint8_t* colours, void* stream);
+// Colours of the pass slots of nsweeps sweeps under the random pass order.
+int launch_slot_colours(uint8_t* out, uint32_t sweep0, uint32_t nsweeps, int passes, const DevRng& rng, void* stream);
 
 // ---- batched chains (tl_batch.cu) ----
 struct BatchChain {

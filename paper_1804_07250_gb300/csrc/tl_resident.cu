@@ -36,7 +36,7 @@ struct ResParams {
     Geom g;
     const int* stripe_lo;
     int halo, npre;
-    int random_order;           // colours of the pass slots drawn per sweep
+    const uint8_t* colours;     // random pass order: colour of every slot of the launch, else nullptr
     int cap_items;              // item-table capacity per CTA
     int cap_cycle;              // random-plane buffer capacity (groups per cycle)
     uint32_t sweep0, nsweeps;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             uint32_t sweep = cyc_sweep, pass = cyc_pass;
             int base = 0;
             for (int i = 1; i <= hc; ++i) {
-                const uint32_t colour = P.random_order ? slot_colour(P.rng, sweep, pass, passes) : pass;
+                const uint32_t colour = P.colours ? P.colours[(size_t)(sweep - P.sweep0) * passes + pass] : pass;
                 const PassRange pr = pass_range<LAT>(g, i, colour, slo, shi, bot, top, off, nloc);
                 s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)(pass | (colour << 8)));
                 s_psweep[i - 1] = sweep;
@@ -251,37 +251,27 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             s_next_pass = pass;
         }
         __syncthreads();
-        // random planes of one pass (generator warps): one thread per
-        // (plane, group) pair, pairs numbered plane-major so that neighbouring
-        // threads write neighbouring 16-byte slots; two Philox calls in flight
-        // per thread.  k = idx / e.y by a multiply-high with ceil(2^32 / e.y)
-        // (too large by at most one, then corrected; e.y = 1 needs none).
+        // random planes of one pass (generator warps): per group, four planes
+        // at a time -- independent Philox chains the scheduler interleaves
+        // (computing all four even when fewer are kept measured faster than
+        // guarding them, and than spreading single planes over threads)
         auto gen = [&](int i) {
             const int4 e = s_ptab[i];
-            if (e.y <= 0) return;
             const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w & 255u;   // slot
-            const uint32_t d = (uint32_t)e.y, mg = 0xFFFFFFFFu / d + 1u;
-            const int n = P.npre * e.y;
-            for (int b0 = rtid; b0 < n; b0 += 2 * HALF) {
-                uint4 o[2];
-                int slot[2];
+            for (int it = rtid; it < e.y; it += HALF) {
+                const uint32_t item = items[e.x + it];
+                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+                for (int k0 = 0; k0 < P.npre; k0 += 4) {
+                    uint4 o[4];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int idx = b0 + q * HALF;
-                    slot[q] = -1;
-                    if (idx >= n) continue;
-                    uint32_t k = d == 1u ? (uint32_t)idx : __umulhi((uint32_t)idx, mg);
-                    if (k * d > (uint32_t)idx) --k;
-                    const int it = idx - (int)(k * d);
-                    const uint32_t item = items[e.x + it];
-                    const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
-                    const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                    o[q] = philox10(grp, sweep, (k << 16) | pass, P.rng.stream, P.rng.k0, P.rng.k1);
-                    slot[q] = (int)k * cap + e.z + it;
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = philox10(grp, sweep, ((uint32_t)(k0 + q) << 16) | pass, P.rng.stream, P.rng.k0,
+                                        P.rng.k1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q < P.npre) rbuf[(size_t)(k0 + q) * cap + e.z + it] = o[q];
                 }
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    if (slot[q] >= 0) rbuf[slot[q]] = o[q];
             }
         };
         if (!upd_role) gen(0);
@@ -311,7 +301,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
 #pragma unroll
                 for (int q = 0; q < MAXI; ++q)
                     if (has[q]) domino_fast_store(r[q]);
-            } else if (upd_role) {
+            } else if (!FAST && upd_role) {
                 for (int it = rtid; it < e.y; it += HALF) {
                     const uint32_t item = items[e.x + it];
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
@@ -474,7 +464,7 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, int random_order, void* stream)
+                    uint32_t stride, const uint8_t* colours, void* stream)
 {
     ResParams P;
     P.rows0 = rows + g.row_words;
@@ -482,7 +472,7 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     P.stripe_lo = plan.stripe_lo;
     P.halo = plan.halo;
     P.npre = plan.npre;
-    P.random_order = random_order;
+    P.colours = colours;
     P.cap_items = plan.cap_items;
     P.cap_cycle = plan.cap_cycle;
     P.sweep0 = sweep0;
@@ -501,6 +491,25 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
     const void* k = pick(g.lattice, th.kind, plan.threads, plan.fast);
     return (int)cudaLaunchCooperativeKernel(k, dim3(plan.ctas), dim3(plan.threads), args, plan.smem_bytes,
                                             reinterpret_cast<cudaStream_t>(stream));
+}
+
+// Colours of the pass slots of sweeps sweep0 .. sweep0 + nsweeps - 1 under
+// the random pass order: out[s * passes + i] for slot i of sweep sweep0 + s.
+__global__ void slot_colours_kernel(uint8_t* __restrict__ out, uint32_t sweep0, uint32_t nsweeps, int passes,
+                                    DevRng rng)
+{
+    const uint64_t n = (uint64_t)nsweeps * passes;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x)
+        out[j] = (uint8_t)slot_colour(rng, sweep0 + (uint32_t)(j / passes), (uint32_t)(j % passes), passes);
+}
+
+int launch_slot_colours(uint8_t* out, uint32_t sweep0, uint32_t nsweeps, int passes, const DevRng& rng, void* stream)
+{
+    const uint64_t n = (uint64_t)nsweeps * passes;
+    const uint64_t blocks = (n + 255) / 256;
+    slot_colours_kernel<<<(unsigned)(blocks < 1024 ? (blocks ? blocks : 1) : 1024), 256, 0,
+                          reinterpret_cast<cudaStream_t>(stream)>>>(out, sweep0, nsweeps, passes, rng);
+    return (int)cudaGetLastError();
 }
 
 }  // namespace tl
