@@ -435,7 +435,7 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     b = T.Batch(ctx, chains)
     stream = torch.cuda.Stream()
-    plan = b.autotune(trial_sweeps=8, stream=stream)
+    plan = b.autotune(trial_sweeps=48, stream=stream)
     b.set_plan(graph_block=BATCH_BLOCK)
     for _ in range(args.warmup):
         b.run(BATCH_BLOCK, stream=stream)

@@ -468,8 +468,9 @@ int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream);
 int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* plan);
 int tl_batch_get_plan(tl_batch* b, tl_batch_plan* plan);
 /* Time every tile height in {32, 64, 128} x R in {1, 2, 4, 8} on the batch
- * itself for `trial_sweeps` sweeps each, keep the fastest plan; states and
- * sweep counters are restored afterwards. */
+ * itself for `trial_sweeps` sweeps (rounded up to a multiple of R), twice
+ * each from the same states, and keep the plan with the fastest run; states
+ * and sweep counters are restored afterwards. */
 int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, tl_batch_plan* out);
 uint64_t tl_batch_launches(const tl_batch* b);
 
