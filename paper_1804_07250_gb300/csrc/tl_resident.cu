@@ -228,54 +228,58 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     uint64_t done = 0;
     int cyc = 0;
     uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
-    while (done < total) {
-        const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
-        // pass table of this cycle: item range, random-plane offset, pass slot
-        // | colour << 8, sweep.  The slot keys the random numbers, the colour
-        // (the slot itself unless the order is random) selects the sites.
-        if (tid == 0) {
-            uint32_t sweep = cyc_sweep, pass = cyc_pass;
-            int base = 0;
-            for (int i = 1; i <= hc; ++i) {
-                const uint32_t colour = P.colours ? P.colours[(size_t)(sweep - P.sweep0) * passes + pass] : pass;
-                const PassRange pr = pass_range<LAT>(g, i, colour, slo, shi, bot, top, off, nloc);
-                s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)(pass | (colour << 8)));
-                s_psweep[i - 1] = sweep;
-                base += pr.e - pr.s;
-                if (++pass == (uint32_t)passes) {
-                    pass = 0;
-                    ++sweep;
-                }
+    // pass table of a cycle: item range, random-plane offset, pass slot |
+    // colour << 8, sweep.  The slot keys the random numbers, the colour (the
+    // slot itself unless the order is random) selects the sites.  Built by
+    // the first generator thread.
+    auto build_table = [&](int hc_, uint32_t sweep, uint32_t pass) {
+        int base = 0;
+        for (int i = 1; i <= hc_; ++i) {
+            const uint32_t colour = P.colours ? P.colours[(size_t)(sweep - P.sweep0) * passes + pass] : pass;
+            const PassRange pr = pass_range<LAT>(g, i, colour, slo, shi, bot, top, off, nloc);
+            s_ptab[i - 1] = make_int4(pr.s, pr.e - pr.s, base, (int)(pass | (colour << 8)));
+            s_psweep[i - 1] = sweep;
+            base += pr.e - pr.s;
+            if (++pass == (uint32_t)passes) {
+                pass = 0;
+                ++sweep;
             }
-            s_next_sweep = sweep;
-            s_next_pass = pass;
         }
-        __syncthreads();
-        // random planes of one pass (generator warps): per group, four planes
-        // at a time -- independent Philox chains the scheduler interleaves
-        // (computing all four even when fewer are kept measured faster than
-        // guarding them, and than spreading single planes over threads)
-        auto gen = [&](int i) {
-            const int4 e = s_ptab[i];
-            const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w & 255u;   // slot
-            for (int it = rtid; it < e.y; it += HALF) {
-                const uint32_t item = items[e.x + it];
-                const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
-                const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
-                for (int k0 = 0; k0 < P.npre; k0 += 4) {
-                    uint4 o[4];
+        s_next_sweep = sweep;
+        s_next_pass = pass;
+    };
+    // random planes of one pass (generator warps): per group, four planes
+    // at a time -- independent Philox chains the scheduler interleaves
+    // (computing all four even when fewer are kept measured faster than
+    // guarding them, and than spreading single planes over threads)
+    auto gen = [&](int i) {
+        const int4 e = s_ptab[i];
+        const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w & 255u;   // slot
+        for (int it = rtid; it < e.y; it += HALF) {
+            const uint32_t item = items[e.x + it];
+            const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
+            const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
+            for (int k0 = 0; k0 < P.npre; k0 += 4) {
+                uint4 o[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        o[q] = philox10(grp, sweep, ((uint32_t)(k0 + q) << 16) | pass, P.rng.stream, P.rng.k0,
-                                        P.rng.k1);
+                for (int q = 0; q < 4; ++q)
+                    o[q] = philox10(grp, sweep, ((uint32_t)(k0 + q) << 16) | pass, P.rng.stream, P.rng.k0,
+                                    P.rng.k1);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (k0 + q < P.npre) rbuf[(size_t)(k0 + q) * cap + e.z + it] = o[q];
-                }
+                for (int q = 0; q < 4; ++q)
+                    if (k0 + q < P.npre) rbuf[(size_t)(k0 + q) * cap + e.z + it] = o[q];
             }
-        };
-        if (!upd_role) gen(0);
-        __syncthreads();
+        }
+    };
+    // the first cycle's table and random planes; later cycles get theirs from
+    // the generator warps while the updater warps exchange boundary rows
+    int hc = (int)(total < (uint64_t)h ? total : (uint64_t)h);
+    if (tid == HALF) build_table(hc, cyc_sweep, cyc_pass);
+    __syncthreads();
+    if (!upd_role) gen(0);
+    __syncthreads();
+    while (true) {
+        const uint32_t next_sweep = s_next_sweep, next_pass = s_next_pass;
         for (int i = 0; i < hc; ++i) {
             const int4 e = s_ptab[i];
             const uint32_t sweep = s_psweep[i], slot = (uint32_t)e.w & 255u, pass = (uint32_t)e.w >> 8;
@@ -347,74 +351,82 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 }
             }
         }
-        cyc_sweep = s_next_sweep;
-        cyc_pass = s_next_pass;
+        cyc_sweep = next_sweep;
+        cyc_pass = next_pass;
         done += (uint64_t)hc;
         if (done >= total) break;
-
-        // ---- exchange: tagged 64-bit words, double-buffered by cycle parity ----
-        const int par = cyc & 1;
-        const unsigned long long tag =
-            ((unsigned long long)(((P.epoch & 0xFFFFu) << 16) | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
-        unsigned long long* mine = P.xbuf + ((size_t)c * 4 + (size_t)par * 2) * side_words;
-        const size_t half = side_words / 2;   // 16-byte units per side (side_words is a multiple of 4)
-        if (!bot) {
-            const uint32_t* src = srow0 + (int64_t)lo * RW;
-            for (size_t w = tid; w < half; w += NT) st_relaxed2(mine + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
-        }
-        if (!top) {
-            const uint32_t* src = srow0 + (int64_t)(hi - h) * RW;
-            for (size_t w = tid; w < half; w += NT)
-                st_relaxed2(mine + side_words + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
-        }
-        // every thread polls its 16-byte units of both sides with loads in flight
-        constexpr int MAXU = 4;
+        const int hc_next = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
         int ok = 1;
-        const uint64_t t_wait = globaltimer();
-        const unsigned long long* th0 = bot ? nullptr : P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words;
-        const unsigned long long* th1 = top ? nullptr : P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
-        uint32_t* d0 = srow0 + (int64_t)(lo - h) * RW;
-        uint32_t* d1 = srow0 + (int64_t)hi * RW;
-        const int units = 2 * (int)half;   // both sides
-        for (int u0 = tid; u0 < units && ok; u0 += MAXU * NT) {
-            unsigned long long a[MAXU], b[MAXU];
-            unsigned need = 0;
-#pragma unroll
-            for (int q = 0; q < MAXU; ++q) {
-                const int u = u0 + q * NT;
-                const bool side = u >= (int)half;
-                const unsigned long long* src = side ? th1 : th0;
-                if (u < units && src != nullptr) {
-                    need |= 1u << q;
-                    ld_relaxed2(src + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
-                }
+        if (!upd_role) {
+            // the next cycle's pass table and first random planes (they touch
+            // no rows, so they overlap the exchange)
+            if (tid == HALF) build_table(hc_next, cyc_sweep, cyc_pass);
+            asm volatile("bar.sync 2, %0;" ::"r"(HALF) : "memory");
+            gen(0);
+        } else {
+            // ---- exchange: tagged 64-bit words, double-buffered by cycle parity ----
+            const int par = cyc & 1;
+            const unsigned long long tag =
+                ((unsigned long long)(((P.epoch & 0xFFFFu) << 16) | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
+            unsigned long long* mine = P.xbuf + ((size_t)c * 4 + (size_t)par * 2) * side_words;
+            const size_t half = side_words / 2;   // 16-byte units per side (side_words is a multiple of 4)
+            if (!bot) {
+                const uint32_t* src = srow0 + (int64_t)lo * RW;
+                for (size_t w = rtid; w < half; w += HALF) st_relaxed2(mine + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
             }
-            while (need) {
-#pragma unroll
+            if (!top) {
+                const uint32_t* src = srow0 + (int64_t)(hi - h) * RW;
+                for (size_t w = rtid; w < half; w += HALF)
+                    st_relaxed2(mine + side_words + 2 * w, tag | src[2 * w], tag | src[2 * w + 1]);
+            }
+            // every updater thread polls its 16-byte units of both sides with loads in flight
+            constexpr int MAXU = 4;
+            const uint64_t t_wait = globaltimer();
+            const unsigned long long* th0 = bot ? nullptr : P.xbuf + ((size_t)(c - 1) * 4 + (size_t)par * 2 + 1) * side_words;
+            const unsigned long long* th1 = top ? nullptr : P.xbuf + ((size_t)(c + 1) * 4 + (size_t)par * 2) * side_words;
+            uint32_t* d0 = srow0 + (int64_t)(lo - h) * RW;
+            uint32_t* d1 = srow0 + (int64_t)hi * RW;
+            const int units = 2 * (int)half;   // both sides
+            for (int u0 = rtid; u0 < units && ok; u0 += MAXU * HALF) {
+                unsigned long long a[MAXU], b[MAXU];
+                unsigned need = 0;
+    #pragma unroll
                 for (int q = 0; q < MAXU; ++q) {
-                    if (!(need >> q & 1u)) continue;
-                    if ((a[q] & 0xFFFFFFFF00000000ull) == tag && (b[q] & 0xFFFFFFFF00000000ull) == tag) {
-                        const int u = u0 + q * NT;
-                        const bool side = u >= (int)half;
-                        uint32_t* d = (side ? d1 : d0) + 2 * (u - (side ? (int)half : 0));
-                        d[0] = (uint32_t)a[q];
-                        d[1] = (uint32_t)b[q];
-                        need &= ~(1u << q);
+                    const int u = u0 + q * HALF;
+                    const bool side = u >= (int)half;
+                    const unsigned long long* src = side ? th1 : th0;
+                    if (u < units && src != nullptr) {
+                        need |= 1u << q;
+                        ld_relaxed2(src + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
                     }
                 }
-                if (!need) break;
-                if (*(volatile int*)P.status || globaltimer() - t_wait > kWaitLimitNs) {
-                    atomicExch(P.status, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-#pragma unroll
-                for (int q = 0; q < MAXU; ++q) {
-                    if (!(need >> q & 1u)) continue;
-                    const int u = u0 + q * NT;
-                    const bool side = u >= (int)half;
-                    ld_relaxed2((side ? th1 : th0) + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
+                while (need) {
+    #pragma unroll
+                    for (int q = 0; q < MAXU; ++q) {
+                        if (!(need >> q & 1u)) continue;
+                        if ((a[q] & 0xFFFFFFFF00000000ull) == tag && (b[q] & 0xFFFFFFFF00000000ull) == tag) {
+                            const int u = u0 + q * HALF;
+                            const bool side = u >= (int)half;
+                            uint32_t* d = (side ? d1 : d0) + 2 * (u - (side ? (int)half : 0));
+                            d[0] = (uint32_t)a[q];
+                            d[1] = (uint32_t)b[q];
+                            need &= ~(1u << q);
+                        }
+                    }
+                    if (!need) break;
+                    if (*(volatile int*)P.status || globaltimer() - t_wait > kWaitLimitNs) {
+                        atomicExch(P.status, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+    #pragma unroll
+                    for (int q = 0; q < MAXU; ++q) {
+                        if (!(need >> q & 1u)) continue;
+                        const int u = u0 + q * HALF;
+                        const bool side = u >= (int)half;
+                        ld_relaxed2((side ? th1 : th0) + 2 * (u - (side ? (int)half : 0)), &a[q], &b[q]);
+                    }
                 }
             }
         }
@@ -423,6 +435,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         if (!ok) s_ok = 0;
         __syncthreads();
         if (!s_ok) return;   // the state is undefined; the host reports TL_ETIMEOUT
+        hc = hc_next;
         ++cyc;
     }
     copy_rows_to_global(P.rows0 + (int64_t)lo * RW, srow0 + (int64_t)lo * RW, (int64_t)(hi - lo) * RW, tid, NT);
