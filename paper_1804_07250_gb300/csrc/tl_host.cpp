@@ -1223,15 +1223,32 @@ static int take_sample(tl_chain* c, void* stream)
 
 // Default halo depth (passes per exchange), threads per CTA and random
 // planes generated ahead for the resident kernel.
-static int default_halo(const Geom& g)
+// Dominoes at t = 2^31 take the single-plane update when it fits.
+static bool fast_candidate(const tl_chain* c)
 {
-    return g.lattice == LAT_DOMINO ? 8 : (g.lattice == LAT_LOZENGE ? 6 : 8);
+    return c->g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
+           c->npre_req <= 1 && !c->no_fast;
 }
+
+// Defaults measured on the Aztec diamond of order 2048, the hexagon 1024^3
+// and the domain-wall square 2048: the single-plane domino update runs
+// fastest with 1024 threads and 6 passes per exchange, the others with 512
+// threads and 8 (dominoes, six-vertex) or 6 (lozenges) passes.
+static int default_halo(const tl_chain* c)
+{
+    if (fast_candidate(c)) return 6;
+    return c->g.lattice == LAT_LOZENGE ? 6 : 8;
+}
+static int default_threads(const tl_chain* c) { return fast_candidate(c) ? 1024 : 512; }
 static int default_npre(const tl_chain* c)
 {
     if (c->th.kind == THR_SCALAR) return c->th.kmax < 0 ? 1 : std::min(8, c->th.kmax + 1);
     return 8;
 }
+
+// Groups one pass of the single-plane domino update can hold: each of the
+// threads / 2 updater threads takes up to two groups (one with 1024 threads).
+static int fast_capacity(int threads) { return (threads / 2) * (threads >= 1024 ? 1 : 2); }
 
 // Local rows of stripe [lo, hi) of `C`, with halo h, clamped to the pads.
 static void stripe_local(int lo, int hi, int k, int C, int h, int H, int* slo, int* shi)
@@ -1245,8 +1262,8 @@ static int plan_resident(tl_chain* c)
 {
     const Geom& g = c->g;
     const tl_domain& d = c->dom_copy;
-    const int h = c->halo_req > 0 ? c->halo_req : default_halo(g);
-    const int threads = c->threads_req > 0 ? c->threads_req : 512;
+    const int h = c->halo_req > 0 ? c->halo_req : default_halo(c);
+    const int threads = c->threads_req > 0 ? c->threads_req : default_threads(c);
     const int npre = c->npre_req > 0 ? c->npre_req : default_npre(c);
     const bool sixv = g.lattice == LAT_SIXV;
     std::vector<int> act(g.H, 0);
@@ -1315,7 +1332,7 @@ static int plan_resident(tl_chain* c)
         }
         const int ntab = sixv ? 2 : 1;
         const bool fast = g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
-                          max_pass <= threads && c->npre_req <= 1 && !c->no_fast;
+                          max_pass <= fast_capacity(threads) && c->npre_req <= 1 && !c->no_fast;
         size_t smem = (size_t)max_nloc * row_bytes + (size_t)npre * cap_cycle * 16 + (size_t)cap_items * 4 +
                       (size_t)ntab * (max_nloc + 1) * 4 + 16;
         if (fast) smem += (size_t)cap_items * 8 + 8;

@@ -316,3 +316,11 @@ def test_device_buffers(T, ctx):
     O.sweeps(O.DOMINO, st, seed=5, k=10, t_scalar=1 << 31)
     assert np.array_equal(out.cpu().numpy(), st)
     assert int(hbuf.cpu().numpy().view(np.uint64)[0]) == O.state_hash(st)
+
+
+@pytest.mark.parametrize("threads", [0, 512, 1024])
+def test_resident_wide_domain_pass_capacity(T, ctx, threads):
+    # a wide, short domain whose passes hold between 512 and 1024 groups per
+    # CTA: more than the single-plane domino update takes, so the plan must
+    # fall back to the general update with either thread count
+    _run_pair(T, ctx, "rect", (8000, 30), seed=61, k=10, kernel=2, threads=threads, scalar=1 << 31)
