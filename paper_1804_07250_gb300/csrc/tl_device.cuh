@@ -553,16 +553,18 @@ TL_DEV uint64_t word_hash(uint32_t w, const Geom& g, int y, int pl, int k)
     return acc;
 }
 
-// Add the set bits of one packed word to the canonical edge counters.
-TL_DEV void word_count(uint32_t w, const Geom& g, int y, int pl, int k, uint32_t* counts)
+// Edge-occupancy counters, bit-sliced in the packed layout: counter bit b
+// of the 32 edges of packed word i (row-major over the H real rows) is bit
+// of word cplanes[b * H * row_words + i].  Adding a word of the state is a
+// ripple-carry add over the planes that stops when no carry is left.
+TL_DEV void word_count_sliced(uint32_t w, int64_t i, int64_t plane_words, uint32_t* cplanes)
 {
-    const int type = pl / g.npar, res = pl - type * g.npar;
-    uint32_t* c = counts + ((size_t)type * g.H + y) * g.W;
-    while (w) {
-        const int b = __ffs(w) - 1;
-        w &= w - 1;
-        const int x = g.npar * (32 * k + b) + res;
-        if (x < g.W) c[x] += 1u;
+    uint32_t carry = w;
+    for (int b = 0; b < 32 && carry; ++b) {
+        uint32_t* p = cplanes + (int64_t)b * plane_words + i;
+        const uint32_t c = *p;
+        *p = c ^ carry;
+        carry &= c;
     }
 }
 

@@ -894,7 +894,8 @@ struct tl_chain {
     uint64_t launches = 0;
     // observables
     unsigned long long* hash = nullptr;
-    uint32_t* counts = nullptr;
+    uint32_t* counts = nullptr;        // canonical counters, decoded at readback
+    uint32_t* cplanes = nullptr;       // bit-sliced counters [32][H][row_words]
     uint64_t samples = 0;
     uint32_t stride = 0;
     uint64_t burn = 0;
@@ -931,6 +932,7 @@ static void chain_free(tl_chain* c)
     cudaFree(c->tplanes);
     cudaFree(c->hash);
     cudaFree(c->counts);
+    cudaFree(c->cplanes);
     cudaFree(c->colours);
     cudaFree(c->hseg);
     cudaFree(c->hbase);
@@ -1214,7 +1216,7 @@ static uint64_t samples_upto(const tl_chain* c, uint64_t x)
 
 static int take_sample(tl_chain* c, void* stream)
 {
-    const int e = launch_density_accumulate(c->g, c->rows, c->counts, stream);
+    const int e = launch_density_accumulate(c->g, c->rows, c->cplanes, stream);
     if (e) return fail(TL_ECUDA, "density kernel: %s", cudaGetErrorString((cudaError_t)e));
     c->samples += 1;
     c->launches += 1;
@@ -1412,7 +1414,7 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
         }
         const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
                                       c->grange, ++c->epoch, ring ? ring + done : nullptr,
-                                      dens ? c->counts : nullptr, c->burn, dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
+                                      dens ? c->cplanes : nullptr, c->burn, dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
         if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
         if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
         c->sweep += n;
@@ -1425,8 +1427,8 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
 static int zero_counts_if_needed(tl_chain* c, void* stream)
 {
     if (c->counts_dirty) {
-        const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
-        CUDA_TRY(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), SS(stream)));
+        const size_t n = (size_t)32 * c->g.H * c->g.row_words;
+        CUDA_TRY(cudaMemsetAsync(c->cplanes, 0, n * sizeof(uint32_t), SS(stream)));
         c->counts_dirty = false;
     }
     return TL_OK;
@@ -1730,6 +1732,7 @@ TL_API int tl_density_begin(tl_chain* c, uint32_t stride, uint64_t burn_in)
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
     if (!c->counts) TL_TRY(dev_alloc(&c->counts, n, "density counters"));
+    if (!c->cplanes) TL_TRY(dev_alloc(&c->cplanes, (size_t)32 * c->g.H * c->g.row_words, "density counter planes"));
     c->counts_dirty = true;
     c->samples = 0;
     c->stride = stride;
@@ -1767,6 +1770,9 @@ TL_API int tl_read_density(tl_chain* c, double* out, size_t cap, uint64_t* sampl
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     TL_TRY(zero_counts_if_needed(c, stream));
     if (samples) *samples = c->samples;
+    const int ed = launch_density_decode(c->g, c->cplanes, c->samples, c->counts, stream);
+    if (ed) return fail(TL_ECUDA, "density decode: %s", cudaGetErrorString((cudaError_t)ed));
+    c->launches += 1;
     return to_output(c, out, n, stream, [&](double* o) {
         return launch_density_read(c->counts, n, c->samples, o, stream);
     });
@@ -1781,6 +1787,9 @@ TL_API int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* strea
     if (cap < n) return fail(TL_EINVAL, "tl_read_domino_nsew: cap %zu < %zu", cap, n);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     TL_TRY(zero_counts_if_needed(c, stream));
+    const int ed = launch_density_decode(c->g, c->cplanes, c->samples, c->counts, stream);
+    if (ed) return fail(TL_ECUDA, "density decode: %s", cudaGetErrorString((cudaError_t)ed));
+    c->launches += 1;
     return to_output(c, out, n, stream, [&](double* o) {
         return launch_nsew(c->g, c->counts, c->samples, c->kappa, o, stream);
     });

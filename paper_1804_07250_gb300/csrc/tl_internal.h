@@ -68,7 +68,10 @@ int launch_unpack(const Geom& g, const uint32_t* rows, uint8_t* canon_dev, void*
 int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t slot, uint32_t sweep,
                        const DevRng& rng, const ThrView& th, const int2* grange, void* stream);
 int launch_hash(const Geom& g, const uint32_t* rows, unsigned long long* out, void* stream);
-int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* counts, void* stream);
+// Density counters are bit-sliced planes [32][H][row_words] (cplanes);
+// launch_density_decode writes the canonical counts [ntype][H][W] from them.
+int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* cplanes, void* stream);
+int launch_density_decode(const Geom& g, const uint32_t* cplanes, uint64_t samples, uint32_t* counts, void* stream);
 int launch_density_read(const uint32_t* counts, uint64_t n, uint64_t samples, double* out,
                         void* stream);
 int launch_nsew(const Geom& g, const uint32_t* counts, uint64_t samples, int kappa, double* out,

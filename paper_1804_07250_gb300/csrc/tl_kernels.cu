@@ -202,25 +202,49 @@ int launch_hash(const Geom& g, const uint32_t* rows, unsigned long long* out, vo
     return (int)cudaGetLastError();
 }
 
-// Edge-occupancy counters in canonical layout: counts[type][y][x] += bit.
-__global__ void density_acc_kernel(const uint32_t* __restrict__ rows0, Geom g, uint32_t* __restrict__ counts)
+// Edge-occupancy counters, bit-sliced in the packed layout (word_count_sliced).
+__global__ void density_acc_kernel(const uint32_t* __restrict__ rows0, Geom g, uint32_t* __restrict__ cplanes)
 {
     const int64_t n = (int64_t)g.H * g.row_words;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t w = rows0[i];
-        if (!w) continue;
-        const int y = (int)(i / g.row_words);
-        const int rem = (int)(i - (int64_t)y * g.row_words);
-        const int pl = rem / g.K, k = rem - pl * g.K;
-        word_count(w, g, y, pl, k, counts);
+        if (w) word_count_sliced(w, i, n, cplanes);
     }
 }
 
-int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* counts, void* stream)
+int launch_density_accumulate(const Geom& g, const uint32_t* rows, uint32_t* cplanes, void* stream)
 {
     const int64_t n = (int64_t)g.H * g.row_words;
-    density_acc_kernel<<<grid_for(n, 256), 256, 0, S(stream)>>>(rows + g.row_words, g, counts);
+    density_acc_kernel<<<grid_for(n, 256), 256, 0, S(stream)>>>(rows + g.row_words, g, cplanes);
+    return (int)cudaGetLastError();
+}
+
+// Canonical counters counts[type][y][x] from the bit-sliced planes; only the
+// `nbits` low planes can be non-zero (samples < 2^nbits).
+__global__ void density_decode_kernel(const uint32_t* __restrict__ cplanes, Geom g, int nbits,
+                                      uint32_t* __restrict__ counts)
+{
+    const int64_t n = (int64_t)g.ntype * g.H * g.W, plane = (int64_t)g.H * g.row_words;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.W);
+        const int64_t r = i / g.W;
+        const int y = (int)(r % g.H), type = (int)(r / g.H);
+        const int res = x % g.npar, j = x / g.npar;
+        const int64_t w = (int64_t)y * g.row_words + (int64_t)(type * g.npar + res) * g.K + (j >> 5);
+        uint32_t v = 0;
+        for (int b = 0; b < nbits; ++b) v |= ((cplanes[(int64_t)b * plane + w] >> (j & 31)) & 1u) << b;
+        counts[i] = v;
+    }
+}
+
+int launch_density_decode(const Geom& g, const uint32_t* cplanes, uint64_t samples, uint32_t* counts, void* stream)
+{
+    int nbits = 0;
+    while (nbits < 32 && (samples >> nbits)) ++nbits;
+    const int64_t n = (int64_t)g.ntype * g.H * g.W;
+    density_decode_kernel<<<grid_for(n, 256), 256, 0, S(stream)>>>(cplanes, g, nbits, counts);
     return (int)cudaGetLastError();
 }
 

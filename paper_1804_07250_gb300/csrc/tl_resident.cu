@@ -46,7 +46,7 @@ struct ResParams {
     unsigned long long* xbuf;   // tagged exchange words
     int* status;
     unsigned long long* ring;
-    uint32_t* counts;
+    uint32_t* counts;           // bit-sliced density counter planes, or nullptr
     uint64_t burn;
     uint32_t stride;
     unsigned int epoch;
@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                         const int rem = w - rr * rw;
                         const int pl = rem / g.K, k = rem - pl * g.K;
                         if (P.ring) acc += word_hash(v, g, lo + rr, pl, k);
-                        if (sample) word_count(v, g, lo + rr, pl, k, P.counts);
+                        if (sample)
+                            word_count_sliced(v, (int64_t)(lo + rr) * rw + rem, (int64_t)g.H * rw, P.counts);
                     }
                     if (P.ring) {
                         for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);

@@ -324,3 +324,29 @@ def test_resident_wide_domain_pass_capacity(T, ctx, threads):
     # CTA: more than the single-plane domino update takes, so the plan must
     # fall back to the general update with either thread count
     _run_pair(T, ctx, "rect", (8000, 30), seed=61, k=10, kernel=2, threads=threads, scalar=1 << 31)
+
+
+@pytest.mark.parametrize("kind,args,kernel", [("aztec", (100,), 2), ("hex", (40, 50, 30), 2), ("hex", (40, 50, 30), 1),
+                                               ("dwbc", (90,), 2)])
+def test_density_counts_many_samples(T, ctx, kind, args, kernel):
+    # one sample every sweep for 300 sweeps: the counters carry through nine
+    # bit planes; counts must equal the oracle's exactly
+    dom = _domain(T, kind, args)
+    lat = _lat(kind)
+    if lat == O.SIXV:
+        t16 = O.sixv_thresholds(SQ2)
+        th, okw = T.thresholds(table16=t16), dict(t16=t16)
+    else:
+        th, okw = T.thresholds(scalar=0x70000000), dict(t_scalar=0x70000000)
+    ch = T.Chain(ctx, dom, seed=8, th=th)
+    ch.set_plan(kernel)
+    ch.density_begin(stride=1, burn_in=0)
+    ch.run(300)
+    dens, samples = ch.read_density()
+    st = _oracle_state(kind, args)
+    counts = np.zeros(st.shape, dtype=np.uint32)
+    for s in range(300):
+        O.sweeps(lat, st, seed=8, sweep0=s, k=1, **okw)
+        O.accumulate(st, counts)
+    assert samples == 300
+    assert np.array_equal(np.rint(dens * 300).astype(np.uint32), counts)
