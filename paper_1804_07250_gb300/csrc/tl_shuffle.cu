@@ -29,6 +29,18 @@ enum : uint8_t { SH_EMPTY = 0, SH_HL = 1, SH_HR = 2, SH_VB = 3, SH_VT = 4 };
 
 TL_DEV bool in_diamond(int x, int y, int k) { return abs(2 * x + 1) + abs(2 * y + 1) <= 2 * k; }
 
+// Cell of this thread: block row blockIdx.y is diamond row y = blockIdx.y - K,
+// whose cells are x in [-w, w) with w = K - |y + 1/2| + 1/2; threads past
+// the row's end return false.
+TL_DEV bool row_cell(int K, int& x, int& y)
+{
+    y = (int)blockIdx.y - K;
+    const int w = K - (y >= 0 ? y : -y - 1);
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    x = t - w;
+    return t < 2 * w;
+}
+
 TL_DEV uint8_t cell_at(const uint8_t* A, int n, int x, int y)
 {
     if (x < -n || y < -n || x >= n || y >= n) return SH_EMPTY;
@@ -47,8 +59,8 @@ TL_DEV bool survives(const uint8_t* A, int n, int k, int ax, int ay, int o)
 __global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __restrict__ B, int n, int k)
 {
     const int K = k + 1;
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x) - K, y = (int)blockIdx.y - K;
-    if (x >= K || !in_diamond(x, y, K)) return;
+    int x, y;
+    if (!row_cell(K, x, y)) return;
     {
         uint8_t out = SH_EMPTY;
         // from below, going north (horizontal)
@@ -83,8 +95,8 @@ __global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __re
 // thread walks down its own run.
 __global__ void shuffle_mark_kernel(const uint8_t* __restrict__ B, uint8_t* __restrict__ F, int n, int K)
 {
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x) - K, y = (int)blockIdx.y - K;
-    if (x >= K || !in_diamond(x, y, K)) return;
+    int x, y;
+    if (!row_cell(K, x, y)) return;
     {
         const size_t c = (size_t)(y + n) * (2 * n) + (x + n);
         uint8_t mark = 0;
@@ -103,8 +115,8 @@ __global__ void shuffle_mark_kernel(const uint8_t* __restrict__ B, uint8_t* __re
 __global__ void shuffle_create_kernel(uint8_t* __restrict__ B, const uint8_t* __restrict__ F, int n, int K,
                                       DevRng rng, uint32_t tbar, int* __restrict__ status)
 {
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x) - K, y = (int)blockIdx.y - K;
-    if (x >= K || !in_diamond(x, y, K)) return;
+    int x, y;
+    if (!row_cell(K, x, y)) return;
     {
         const size_t c = (size_t)(y + n) * (2 * n) + (x + n);
         if (!F[c]) return;
