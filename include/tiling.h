@@ -463,7 +463,10 @@ int tl_batch_run(tl_batch* b, uint64_t k, void* stream);
 /* The comparison point: the same kernel launched once per chain per R
  * sweeps (no batching, no graph). */
 int tl_batch_run_per_chain(tl_batch* b, uint64_t k, void* stream);
-/* State hash of every chain (uint64 out[n], host or device, n >= chains). */
+/* State hash of every chain (uint64 out[n], host or device, n >= chains).
+ * With a host `out` the call waits for the stream and reports TL_ETIMEOUT if
+ * a batch launch gave up waiting for a tile's bulk copy (bounded at two
+ * seconds; the chain states are then undefined). */
 int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream);
 int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* plan);
 int tl_batch_get_plan(tl_batch* b, tl_batch_plan* plan);

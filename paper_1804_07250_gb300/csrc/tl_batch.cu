@@ -16,6 +16,60 @@
 
 namespace tl {
 
+// Bulk asynchronous copies (the copy engine of sm_90+, cp.async.bulk) between
+// global and shared memory, completed through an mbarrier (loads) or a bulk
+// group (stores).  Addresses 16-byte aligned, sizes multiples of 16 bytes.
+TL_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+TL_DEV void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+TL_DEV void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+TL_DEV bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+TL_DEV uint64_t batch_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `parity` to complete, at most about two seconds.
+TL_DEV bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity)
+{
+    const uint64_t t0 = batch_globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && batch_globaltimer() - t0 > 2000000000ull) return false;
+    }
+}
+TL_DEV void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+TL_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+TL_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+TL_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 template <int LAT, int TK>
 TL_DEV void tile_passes(const BatchChain& ch, uint32_t* srow0, int slo, int shi, bool bot, bool top, uint32_t sweep0,
                         int R)
@@ -59,11 +113,16 @@ TL_DEV void tile_passes(const BatchChain& ch, uint32_t* srow0, int slo, int shi,
 
 __global__ void __launch_bounds__(256) batch_kernel(const BatchChain* __restrict__ chains,
                                                     const BatchTile* __restrict__ tiles, int ntiles, int R,
-                                                    uint32_t sweep_off, int src, unsigned int* cursor)
+                                                    uint32_t sweep_off, int src, unsigned int* cursor,
+                                                    int* __restrict__ status)
 {
     extern __shared__ uint4 smem4[];
     __shared__ int s_tile;
+    __shared__ __align__(8) unsigned long long s_bar;
     uint32_t* sm = reinterpret_cast<uint32_t*>(smem4);
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(cursor, 1u);
         __syncthreads();
@@ -82,13 +141,17 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchChain* __restrict
         const bool bot_x = slo == -1, top_x = shi == g.H + 1;
         const uint32_t* srcp = ch.rows[src] + RW;   // global row 0
         uint32_t* dstp = ch.rows[src ^ 1] + RW;
-        {
-            const uint4* s4 = reinterpret_cast<const uint4*>(srcp + (int64_t)slo * RW);
-            uint4* d4 = reinterpret_cast<uint4*>(sm);
-            const int64_t n4 = (int64_t)(shi - slo) * RW / 4;
-            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldcg(s4 + i);
+        // the tile and its halo rows are contiguous: one bulk copy into shared
+        // memory (rows are whole 16-byte units, buffers 256-byte aligned)
+        if (threadIdx.x == 0) bulk_load(sm, srcp + (int64_t)slo * RW, (uint32_t)((int64_t)(shi - slo) * RW * 4), &s_bar);
+        const int arrived = __syncthreads_and(mbar_wait_bounded(&s_bar, parity) ? 1 : 0);
+        parity ^= 1u;
+        if (!arrived) {
+            // the copy did not complete in two seconds: report and stop (every
+            // thread of the block takes this branch together)
+            if (threadIdx.x == 0) atomicExch(status, 1);
+            return;
         }
-        __syncthreads();
         const uint32_t sweep0 = *ch.sweep_base + sweep_off;
         uint32_t* srow0 = sm - (int64_t)slo * RW;
         if (g.lattice == LAT_DOMINO) {
@@ -100,15 +163,19 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchChain* __restrict
         } else {
             tile_passes<LAT_SIXV, THR_TABLE>(ch, srow0, slo, shi, bot_x, top_x, sweep0, R);
         }
-        {
-            const uint4* s4 = reinterpret_cast<const uint4*>(srow0 + (int64_t)tile.lo * RW);
-            uint4* d4 = reinterpret_cast<uint4*>(dstp + (int64_t)tile.lo * RW);
-            const int64_t n4 = (int64_t)(tile.hi - tile.lo) * RW / 4;
-            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) __stcg(d4 + i, s4[i]);
+        // the tile's own rows back in one bulk copy; shared memory is reused
+        // by the next tile once the copy has read it
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_store(dstp + (int64_t)tile.lo * RW, srow0 + (int64_t)tile.lo * RW,
+                       (uint32_t)((int64_t)(tile.hi - tile.lo) * RW * 4));
+            bulk_wait_read();
         }
         // the pad rows of the destination stay zero: they are never written
         __syncthreads();
     }
+    if (threadIdx.x == 0) bulk_wait_all();
 }
 
 __global__ void batch_advance_kernel(const BatchChain* __restrict__ chains, int nchains, uint32_t k,
@@ -132,10 +199,10 @@ int batch_prepare(size_t smem_bytes, int* blocks_per_sm)
 }
 
 int launch_batch(const BatchChain* chains, const BatchTile* tiles, int ntiles, int R, uint32_t sweep_off, int src,
-                 unsigned int* cursor, int grid, size_t smem_bytes, void* stream)
+                 unsigned int* cursor, int grid, size_t smem_bytes, int* status, void* stream)
 {
     batch_kernel<<<grid, 256, smem_bytes, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles, R,
-                                                                                   sweep_off, src, cursor);
+                                                                                   sweep_off, src, cursor, status);
     return (int)cudaGetLastError();
 }
 

@@ -1815,6 +1815,7 @@ struct tl_batch {
     unsigned int* d_cursor = nullptr;     // one cursor per launch slot
     int ncursor = 0;
     unsigned long long* d_hash = nullptr;
+    int* d_status = nullptr;              // raised by a bounded wait that gave up
     int tile_rows = 64, R = 2, block = 100, grid = 0;
     size_t smem = 0;
     int ntiles = 0;
@@ -1844,6 +1845,7 @@ static void batch_free(tl_batch* b)
     cudaFreeHost(b->h_sweep);
     cudaFree(b->d_cursor);
     cudaFree(b->d_hash);
+    cudaFree(b->d_status);
     delete b;
 }
 
@@ -1969,7 +1971,9 @@ TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_ba
     b->ctx = ctx;
     b->ncursor = 1024;
     int rc = dev_alloc(&b->d_cursor, (size_t)b->ncursor, "cursors");
-    if (rc == TL_OK && cudaMemset(b->d_cursor, 0, sizeof(unsigned int) * b->ncursor) != cudaSuccess)
+    if (rc == TL_OK) rc = dev_alloc(&b->d_status, 1, "status");
+    if (rc == TL_OK && (cudaMemset(b->d_cursor, 0, sizeof(unsigned int) * b->ncursor) != cudaSuccess ||
+                        cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess))
         rc = fail(TL_ECUDA, "tl_batch_create: memset");
     for (size_t i = 0; i < n && rc == TL_OK; ++i) rc = batch_attach(b, chains[i]);
     if (rc == TL_OK) rc = batch_rebuild(b);
@@ -2032,7 +2036,8 @@ static int batch_launch(tl_batch* b, int r, uint32_t off, int slot, void* stream
     unsigned int* cur = b->d_cursor + (slot % b->ncursor);
     if (!per_chain) {
         CUDA_TRY(cudaMemsetAsync(cur, 0, 4, SS(stream)));
-        const int e = launch_batch(b->d_chains, b->d_tiles_lpt, b->ntiles, r, off, b->src, cur, b->grid, b->smem, stream);
+        const int e = launch_batch(b->d_chains, b->d_tiles_lpt, b->ntiles, r, off, b->src, cur, b->grid, b->smem,
+                                   b->d_status, stream);
         if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
         b->launches += 1;
     } else {
@@ -2041,7 +2046,7 @@ static int batch_launch(tl_batch* b, int r, uint32_t off, int slot, void* stream
             unsigned int* ci = b->d_cursor + ((slot * (int)b->chains.size() + (int)i) % b->ncursor);
             CUDA_TRY(cudaMemsetAsync(ci, 0, 4, SS(stream)));
             const int e = launch_batch(b->d_chains, b->d_tiles_chain + t0, nt, r, off, b->src, ci,
-                                       std::min(nt, b->grid), b->smem, stream);
+                                       std::min(nt, b->grid), b->smem, b->d_status, stream);
             if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
             b->launches += 1;
         }
@@ -2176,7 +2181,12 @@ TL_API int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream)
     const bool dev = is_device_ptr(out);
     CUDA_TRY(cudaMemcpyAsync(out, b->d_hash, 8 * b->chains.size(), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              SS(stream)));
-    if (!dev) CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    if (!dev) {
+        CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+        int st = 0;
+        CUDA_TRY(cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) return fail(TL_ETIMEOUT, "batch: a tile's bulk copy did not complete; chain states are undefined");
+    }
     return TL_OK;
 }
 
