@@ -1577,7 +1577,8 @@ TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_i
                             void* stream)
 {
     if (!ctx || !canon || n < 1 || n > 32767) return fail(TL_EINVAL, "tl_aztec_shuffle: bad argument");
-    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W, ncell = (size_t)4 * n * n;
+    // cell buffers: 2n rows of 2n bytes rounded up to 4
+    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W, ncell = (size_t)2 * n * ((2 * (size_t)n + 3) & ~(size_t)3);
     if (cap < ncanon) return fail(TL_EINVAL, "tl_aztec_shuffle: cap %zu < %zu", cap, ncanon);
     CUDA_TRY(cudaSetDevice(ctx->device));
     uint8_t *A = nullptr, *B = nullptr, *F = nullptr, *out = nullptr;
@@ -1585,7 +1586,7 @@ TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_i
     const bool dev = is_device_ptr(canon);
     int rc;
     if ((rc = dev_alloc(&A, ncell, "shuffle cells")) || (rc = dev_alloc(&B, ncell, "shuffle cells")) ||
-        (rc = dev_alloc(&F, ncell, "shuffle marks")) || (rc = dev_alloc(&status, 1, "status")) ||
+        (rc = dev_alloc(&F, ncell, "shuffle cells")) || (rc = dev_alloc(&status, 1, "status")) ||
         (!dev && (rc = dev_alloc(&out, ncanon, "shuffle output")))) {
         cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(status); cudaFree(out);
         return rc;
@@ -1595,6 +1596,7 @@ TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_i
     uint64_t launches = 0;
     cudaError_t e = cudaMemsetAsync(A, 0, ncell, SS(stream));
     if (e == cudaSuccess) e = cudaMemsetAsync(B, 0, ncell, SS(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, ncell, SS(stream));
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), SS(stream));
     if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, ncanon, SS(stream));
     if (e == cudaSuccess) e = (cudaError_t)launch_shuffle(n, A, B, F, rng, status, dst, &launches, stream);

@@ -70,7 +70,8 @@ def frozen_fraction(st, n, win=16, level=0.98):
     return float(((frac >= level) & inside).sum() / inside.sum()), t
 
 
-@pytest.mark.parametrize("n,seed,stream", [(1, 0, 0), (2, 5, 1), (7, 11, 2), (40, 3, 9), (129, 8, 4)])
+@pytest.mark.parametrize("n,seed,stream", [(1, 0, 0), (2, 5, 1), (3, 2, 0), (7, 11, 2), (40, 3, 9), (129, 8, 4),
+                                           (201, 6, 7)])
 def test_shuffle_matches_oracle(T, ctx, n, seed, stream):
     got = T.aztec_shuffle(ctx, n, seed=seed, stream_id=stream)
     want = O.aztec_shuffle(n, seed, stream)
