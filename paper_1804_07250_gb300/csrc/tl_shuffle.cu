@@ -18,8 +18,9 @@
 //     all it reads lies in the 3 x 3 cells around it;
 //  2. fill: the cells left empty form disjoint 2x2 blocks whose lower-left
 //     cells have x + y + k + 1 odd, stacked from the bottom of every run of
-//     empty cells in a column.  An empty cell finds its block from the
-//     parity of the run below it and that lower-left parity, and takes its
+//     empty cells in a column.  An empty cell finds its block from its 3 x 3
+//     neighbourhood, or where that allows two blocks, from the parity of the
+//     run below it and that lower-left parity, and takes its
 //     part of the pair the block's Philox draw picks (two horizontal
 //     dominoes below 2^31, else two vertical ones).  The result goes to a
 //     third buffer, so no thread sees another's output.
@@ -58,15 +59,10 @@ TL_DEV uint32_t word_at(const uint8_t* A, int n, int S, int r, int wi)
 
 TL_DEV uint8_t byte_of(uint32_t w, int i) { return (uint8_t)(w >> (8 * i)); }
 
-__global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __restrict__ B, int n, int k)
+// Cells 4 wi - 1 .. 4 wi + 4 of buffer rows r - 1, r, r + 1: cw[1 + dy][1 + i + dx]
+// is the cell (dx, dy) away from cell i of word wi.
+TL_DEV void load_window(const uint8_t* A, int n, int S, int r, int wi, uint8_t (&cw)[3][6])
 {
-    const int K = k + 1, S = cell_pitch(n);
-    int wi, y;
-    if (!row_word(n, K, wi, y)) return;
-    const int r = y + n;
-    // cells 4 wi - 1 .. 4 wi + 4 of rows y - 1, y, y + 1: cw[1 + dy][1 + i + dx]
-    // is the cell (dx, dy) away from cell i of the word
-    uint8_t cw[3][6];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const uint32_t a = word_at(A, n, S, r - 1 + d, wi - 1), b = word_at(A, n, S, r - 1 + d, wi),
@@ -76,6 +72,16 @@ __global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __re
         for (int i = 0; i < 4; ++i) cw[d][1 + i] = byte_of(b, i);
         cw[d][5] = byte_of(c, 0);
     }
+}
+
+__global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __restrict__ B, int n, int k)
+{
+    const int K = k + 1, S = cell_pitch(n);
+    int wi, y;
+    if (!row_word(n, K, wi, y)) return;
+    const int r = y + n;
+    uint8_t cw[3][6];
+    load_window(A, n, S, r, wi, cw);
     uint32_t outw = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -125,24 +131,45 @@ __global__ void shuffle_fill_kernel(const uint8_t* __restrict__ B, uint8_t* __re
     const int r = y + n;
     const uint32_t bw = word_at(B, n, S, r, wi);
     uint32_t outw = bw;
+    bool any = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int x = 4 * wi + i - n;
-        if (byte_of(bw, i) != SH_EMPTY || !in_diamond(x, y, K)) continue;
-        // the run of empty cells below this one in its column
-        int below = 0;
-        for (int yy = y - 1; yy >= -K && in_diamond(x, yy, K) && cell_at(B, n, S, x, yy) == SH_EMPTY; --yy)
-            ++below;
-        const int by = (below & 1) ? y - 1 : y;
-        const int bx = ((x + by + K) & 1) ? x : x - 1;
-        if (x == bx && y == by &&
-            (x + 1 >= n || y + 1 >= n || cell_at(B, n, S, x + 1, y) != SH_EMPTY ||
-             cell_at(B, n, S, x, y + 1) != SH_EMPTY || cell_at(B, n, S, x + 1, y + 1) != SH_EMPTY))
-            atomicExch(status, 1);   // not a 2x2 hole: cannot happen for a valid tiling
-        const uint4 o = philox10(((uint32_t)(by + n) << 16) | (uint32_t)(bx + n), (uint32_t)K, 0xFFFE0000u,
-                                 rng.stream, rng.k0, rng.k1);
-        const uint8_t v = o.x < tbar ? (x > bx ? SH_HR : SH_HL) : (y > by ? SH_VT : SH_VB);
-        outw = (outw & ~(0xFFu << (8 * i))) | ((uint32_t)v << (8 * i));
+    for (int i = 0; i < 4; ++i) any |= byte_of(bw, i) == SH_EMPTY && in_diamond(4 * wi + i - n, y, K);
+    if (any) {
+        uint8_t cw[3][6];
+        load_window(B, n, S, r, wi, cw);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = 4 * wi + i - n;
+            if (cw[1][1 + i] != SH_EMPTY || !in_diamond(x, y, K)) continue;
+            // The block holding this cell has its lower-left corner at (x, y)
+            // or (x - 1, y - 1) if x + y + K is odd, else at (x - 1, y) or
+            // (x, y - 1).  When only one of the two has its other three cells
+            // empty, that is the block; otherwise the parity of the run of
+            // empty cells below this one in its column decides.
+            auto hole = [&](int dx, int dy) {
+                return in_diamond(x + dx, y + dy, K) && cw[1 + dy][1 + i + dx] == SH_EMPTY;
+            };
+            const bool odd = ((x + y + K) & 1) == 1;
+            const bool h1 = odd ? hole(1, 0) && hole(0, 1) && hole(1, 1) : hole(-1, 0) && hole(-1, 1) && hole(0, 1);
+            const bool h2 = odd ? hole(-1, 0) && hole(0, -1) && hole(-1, -1) : hole(0, -1) && hole(1, -1) && hole(1, 0);
+            int bx, by;
+            if (h1 != h2) {
+                bx = odd ? (h1 ? x : x - 1) : (h1 ? x - 1 : x);
+                by = h1 ? y : y - 1;
+            } else {
+                int below = 0;
+                for (int yy = y - 1; yy >= -K && in_diamond(x, yy, K) && cell_at(B, n, S, x, yy) == SH_EMPTY; --yy)
+                    ++below;
+                by = (below & 1) ? y - 1 : y;
+                bx = ((x + by + K) & 1) ? x : x - 1;
+            }
+            if (x == bx && y == by && (x + 1 >= n || y + 1 >= n || !hole(1, 0) || !hole(0, 1) || !hole(1, 1)))
+                atomicExch(status, 1);   // not a 2x2 hole: cannot happen for a valid tiling
+            const uint4 o = philox10(((uint32_t)(by + n) << 16) | (uint32_t)(bx + n), (uint32_t)K, 0xFFFE0000u,
+                                     rng.stream, rng.k0, rng.k1);
+            const uint8_t v = o.x < tbar ? (x > bx ? SH_HR : SH_HL) : (y > by ? SH_VT : SH_VB);
+            outw = (outw & ~(0xFFu << (8 * i))) | ((uint32_t)v << (8 * i));
+        }
     }
     reinterpret_cast<uint32_t*>(C + (size_t)r * S)[wi] = outw;
 }
