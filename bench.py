@@ -549,6 +549,7 @@ def run_serve(args):
 # coupling from the past on the Aztec diamond of order 128 (uniform).
 # ---------------------------------------------------------------------------
 EXACT = {"shuffle2048": ("aztec_diamond_n2048_domino_shuffling", 2048),
+         "shuffle512": ("aztec_diamond_n512_domino_shuffling", 512),
          "cftp_aztec128": ("aztec_diamond_n128_coupling_from_the_past", 128)}
 
 

@@ -301,7 +301,11 @@ int tl_chain_seek(tl_chain* c, uint64_t sweep);
  * seed, counter = ((y+n) << 16 | (x+n), K, 0xFFFE0000, stream_id)): two
  * horizontal dominoes if it is below 2^31, else two vertical ones.  Writes
  * the canonical state of tl_domain_aztec(n) to `canon` (host or device, cap
- * >= 2 (2n+1)^2).  Synchronous.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+ * >= 2 (2n+1)^2).  Synchronous.  The context keeps the device buffers
+ * (about 20 n^2 bytes) and one captured graph of the whole sample
+ * for the last order used, until tl_ctx_destroy or a call with another
+ * order; calls on one context are serialised.  Errors: TL_EINVAL,
+ * TL_ENOMEM, TL_ECUDA. */
 int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_id, uint8_t* canon, size_t cap,
                      void* stream);
 

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,11 +55,31 @@ TL_API const char* tl_version(void) { return "tiling-gb300 0.1 (sm_103a)"; }
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
+// Domino shuffling of one order n, kept per context: the device buffers and
+// one instantiated graph of the whole sample (zeroing, 2n + 1 kernels), so a
+// sample costs one graph launch instead of 2n + 1 host launches.  The key is
+// read by the kernels from `rng`, written before each launch.
+struct ShuffleCache {
+    int n = 0;
+    uint8_t *A = nullptr, *B = nullptr, *F = nullptr, *canon = nullptr;
+    int* status = nullptr;
+    DevRng* rng = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(canon); cudaFree(status); cudaFree(rng);
+        *this = ShuffleCache();
+    }
+};
+
 struct tl_ctx {
     int device;
     int sms;
     int smem_optin;
     int l2_bytes;
+    std::mutex shuffle_mu;   // one shuffling sample at a time per context
+    ShuffleCache shuffle;
 };
 
 TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
@@ -79,7 +100,16 @@ TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
     return TL_OK;
 }
 
-TL_API void tl_ctx_destroy(tl_ctx* c) { delete c; }
+TL_API void tl_ctx_destroy(tl_ctx* c)
+{
+    if (!c) return;
+    if (c->shuffle.n) {
+        cudaSetDevice(c->device);
+        cudaDeviceSynchronize();
+        c->shuffle.release();
+    }
+    delete c;
+}
 
 // ---------------------------------------------------------------------------
 // Domains
@@ -1573,38 +1603,68 @@ TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
     return TL_OK;
 }
 
+// Buffers and graph of order n (rebuilt when n changes).
+static int shuffle_prepare(tl_ctx* ctx, int n)
+{
+    ShuffleCache& sc = ctx->shuffle;
+    if (sc.n == n && sc.exec) return TL_OK;
+    CUDA_TRY(cudaDeviceSynchronize());
+    sc.release();
+    // cell buffers: 2n rows of 2n bytes rounded up to 4
+    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W,
+                 ncell = (size_t)2 * n * ((2 * (size_t)n + 3) & ~(size_t)3);
+    int rc;
+    if ((rc = dev_alloc(&sc.A, ncell, "shuffle cells")) || (rc = dev_alloc(&sc.B, ncell, "shuffle cells")) ||
+        (rc = dev_alloc(&sc.F, ncell, "shuffle cells")) || (rc = dev_alloc(&sc.canon, ncanon, "shuffle output")) ||
+        (rc = dev_alloc(&sc.status, 1, "status")) || (rc = dev_alloc(&sc.rng, 1, "shuffle key"))) {
+        sc.release();
+        return rc;
+    }
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ec = cudaMemsetAsync(sc.A, 0, ncell, cs);
+        if (ec == cudaSuccess) ec = cudaMemsetAsync(sc.B, 0, ncell, cs);
+        if (ec == cudaSuccess) ec = cudaMemsetAsync(sc.F, 0, ncell, cs);
+        if (ec == cudaSuccess) ec = cudaMemsetAsync(sc.status, 0, sizeof(int), cs);
+        if (ec == cudaSuccess) ec = cudaMemsetAsync(sc.canon, 0, ncanon, cs);
+        if (ec == cudaSuccess) ec = (cudaError_t)launch_shuffle(n, sc.A, sc.B, sc.F, sc.rng, sc.status, sc.canon, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = ec;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sc.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sc.release();
+        return fail(TL_ECUDA, "tl_aztec_shuffle: graph of order %d: %s", n, cudaGetErrorString(e));
+    }
+    sc.n = n;
+    return TL_OK;
+}
+
 TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_id, uint8_t* canon, size_t cap,
                             void* stream)
 {
     if (!ctx || !canon || n < 1 || n > 32767) return fail(TL_EINVAL, "tl_aztec_shuffle: bad argument");
-    // cell buffers: 2n rows of 2n bytes rounded up to 4
-    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W, ncell = (size_t)2 * n * ((2 * (size_t)n + 3) & ~(size_t)3);
+    const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W;
     if (cap < ncanon) return fail(TL_EINVAL, "tl_aztec_shuffle: cap %zu < %zu", cap, ncanon);
     CUDA_TRY(cudaSetDevice(ctx->device));
-    uint8_t *A = nullptr, *B = nullptr, *F = nullptr, *out = nullptr;
-    int* status = nullptr;
-    const bool dev = is_device_ptr(canon);
-    int rc;
-    if ((rc = dev_alloc(&A, ncell, "shuffle cells")) || (rc = dev_alloc(&B, ncell, "shuffle cells")) ||
-        (rc = dev_alloc(&F, ncell, "shuffle cells")) || (rc = dev_alloc(&status, 1, "status")) ||
-        (!dev && (rc = dev_alloc(&out, ncanon, "shuffle output")))) {
-        cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(status); cudaFree(out);
-        return rc;
-    }
-    uint8_t* dst = dev ? canon : out;
-    DevRng rng{(uint32_t)seed, (uint32_t)(seed >> 32), stream_id};
-    uint64_t launches = 0;
-    cudaError_t e = cudaMemsetAsync(A, 0, ncell, SS(stream));
-    if (e == cudaSuccess) e = cudaMemsetAsync(B, 0, ncell, SS(stream));
-    if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, ncell, SS(stream));
-    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), SS(stream));
-    if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, ncanon, SS(stream));
-    if (e == cudaSuccess) e = (cudaError_t)launch_shuffle(n, A, B, F, rng, status, dst, &launches, stream);
+    std::lock_guard<std::mutex> lock(ctx->shuffle_mu);
+    TL_TRY(shuffle_prepare(ctx, n));
+    ShuffleCache& sc = ctx->shuffle;
+    const DevRng rng{(uint32_t)seed, (uint32_t)(seed >> 32), stream_id};
     int hstatus = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, SS(stream));
-    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(canon, out, ncanon, cudaMemcpyDeviceToHost, SS(stream));
+    cudaError_t e = cudaMemcpyAsync(sc.rng, &rng, sizeof(rng), cudaMemcpyHostToDevice, SS(stream));
+    if (e == cudaSuccess) e = cudaGraphLaunch(sc.exec, SS(stream));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, sc.status, sizeof(int), cudaMemcpyDeviceToHost, SS(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(canon, sc.canon, ncanon, is_device_ptr(canon) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            SS(stream));
     if (e == cudaSuccess) e = cudaStreamSynchronize(SS(stream));
-    cudaFree(A); cudaFree(B); cudaFree(F); cudaFree(status); cudaFree(out);
     if (e != cudaSuccess) return fail(TL_ECUDA, "tl_aztec_shuffle: %s", cudaGetErrorString(e));
     if (hstatus) return fail(TL_ECUDA, "tl_aztec_shuffle: a created block was not a 2x2 hole");
     return TL_OK;

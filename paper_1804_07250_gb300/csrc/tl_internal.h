@@ -76,11 +76,12 @@ int launch_density_read(const uint32_t* counts, uint64_t n, uint64_t samples, do
                         void* stream);
 int launch_nsew(const Geom& g, const uint32_t* counts, uint64_t samples, int kappa, double* out,
                 void* stream);
-// Domino shuffling of the Aztec diamond of order n: A, B, F are device
-// scratch of (2n)^2 bytes each (A zeroed), canon the zeroed [2][2n+1][2n+1]
-// output; status is raised if a created block is not a 2x2 hole.
-int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng& rng, int* status, uint8_t* canon,
-                   uint64_t* launches, void* stream);
+// Domino shuffling of the Aztec diamond of order n: A, B, F are zeroed
+// device scratch of 2n rows of (2n rounded up to 4) bytes each, rng a device
+// copy of the key, canon the zeroed [2][2n+1][2n+1] output; status is raised
+// if a created block is not a 2x2 hole.  Capturable into a graph.
+int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng* rng, int* status, uint8_t* canon,
+                   void* stream);
 // seg: [nseg][6] height segments (y, lo, hi, parent, xs, dir); base_scratch: nseg ints.
 int launch_height(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
                   int32_t* out, int* base_scratch, void* stream);

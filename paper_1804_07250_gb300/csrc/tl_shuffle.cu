@@ -122,8 +122,10 @@ TL_DEV uint8_t cell_at(const uint8_t* A, int n, int S, int x, int y)
 }
 
 // B (after the move, order K) -> C with every hole filled.
+// `rngp`: the Philox key and stream, read from device memory so that one
+// captured graph of the whole sample serves every seed.
 __global__ void shuffle_fill_kernel(const uint8_t* __restrict__ B, uint8_t* __restrict__ C, int n, int K,
-                                    DevRng rng, uint32_t tbar, int* __restrict__ status)
+                                    const DevRng* __restrict__ rngp, uint32_t tbar, int* __restrict__ status)
 {
     const int S = cell_pitch(n);
     int wi, y;
@@ -135,6 +137,7 @@ __global__ void shuffle_fill_kernel(const uint8_t* __restrict__ B, uint8_t* __re
 #pragma unroll
     for (int i = 0; i < 4; ++i) any |= byte_of(bw, i) == SH_EMPTY && in_diamond(4 * wi + i - n, y, K);
     if (any) {
+        const DevRng rng = *rngp;
         uint8_t cw[3][6];
         load_window(B, n, S, r, wi, cw);
 #pragma unroll
@@ -197,9 +200,11 @@ static int grid_for_cells(int64_t n)
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-// A, B, F: three zeroed buffers of 2n rows of (2n rounded up to 4) bytes.
-int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng& rng, int* status, uint8_t* canon,
-                   uint64_t* launches, void* stream)
+// A, B, F: three zeroed buffers of 2n rows of (2n rounded up to 4) bytes;
+// rng: device copy of the key.  Enqueues 2n + 1 kernels (also under stream
+// capture).
+int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng* rng, int* status, uint8_t* canon,
+                   void* stream)
 {
     const cudaStream_t s = SS_(stream);
     uint8_t *cur = A, *mid = B, *spare = F;
@@ -215,7 +220,6 @@ int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng& rng,
         spare = t;
     }
     shuffle_canon_kernel<<<grid_for_cells((int64_t)4 * n * n), 256, 0, s>>>(cur, n, canon);
-    *launches += (uint64_t)2 * n + 1;
     return (int)cudaGetLastError();
 }
 

@@ -78,6 +78,14 @@ def test_shuffle_matches_oracle(T, ctx, n, seed, stream):
     assert np.array_equal(got, want)
 
 
+def test_shuffle_graph_reused_across_seeds_and_orders(T, ctx):
+    # the context keeps one graph per order: same order with new seeds, and
+    # a change of order and back, all still match the oracle
+    for n, seed, stream in [(40, 1, 0), (40, 2, 0), (40, 2, 5), (7, 3, 1), (40, 4, 2)]:
+        got = T.aztec_shuffle(ctx, n, seed=seed, stream_id=stream)
+        assert np.array_equal(got, O.aztec_shuffle(n, seed, stream))
+
+
 def test_shuffle_large_is_a_tiling_with_the_arctic_circle(T, ctx):
     n = 2048
     st = T.aztec_shuffle(ctx, n, seed=2024, stream_id=0)
