@@ -944,7 +944,6 @@ struct tl_chain {
     unsigned long long* xbuf_d = nullptr;
     int* status_d = nullptr;
     int threads_req = 0, npre_req = 0;
-    bool no_fast = false;
     int random_order = 0;   // colours of the pass slots drawn per sweep
     uint8_t* colours = nullptr;   // device colours of one resident launch's slots
     size_t colours_cap = 0;
@@ -1259,7 +1258,7 @@ static int take_sample(tl_chain* c, void* stream)
 static bool fast_candidate(const tl_chain* c)
 {
     return c->g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
-           c->npre_req <= 1 && !c->no_fast;
+           c->npre_req <= 1;
 }
 
 // Defaults measured on the Aztec diamond of order 2048, the hexagon 1024^3
@@ -1364,7 +1363,7 @@ static int plan_resident(tl_chain* c)
         }
         const int ntab = sixv ? 2 : 1;
         const bool fast = g.lattice == LAT_DOMINO && c->th.kind == THR_SCALAR && c->th.scalar == 0x80000000u &&
-                          max_pass <= fast_capacity(threads) && c->npre_req <= 1 && !c->no_fast;
+                          max_pass <= fast_capacity(threads) && c->npre_req <= 1;
         size_t smem = (size_t)max_nloc * row_bytes + (size_t)npre * cap_cycle * 16 + (size_t)cap_items * 4 +
                       (size_t)ntab * (max_nloc + 1) * 4 + 16;
         if (fast) smem += (size_t)cap_items * 8 + 8;
