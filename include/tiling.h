@@ -364,16 +364,19 @@ int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream);
  * when they need the heights, e.g. code under a device-memory budget that
  * forbids new allocations, or a loop that must not pay the device-wide
  * synchronisation cudaMalloc / cudaFree can cause).  Same result as
- * tl_read_height, but `out` must be device memory (TL_EINVAL otherwise), and
- * the per-row scratch that tl_read_height keeps in chain-owned memory lives
- * in one static device array of 65536 ints (256 KiB) that every GPU using
- * the library holds until the process exits; domains with more height rows
- * are rejected with TL_EINVAL.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress): make the first call on each
- * device before any stream capture.  All calls on a device share the array
- * and each rewrites the entries it uses, so calls whose work overlaps on the
- * GPU (different streams, concurrently) race and must be serialised by the
- * caller.  Enqueues on `stream` only. */
+ * tl_read_height, but `out` must be device memory of the chain's GPU
+ * (TL_EINVAL otherwise), and the per-segment scratch that tl_read_height
+ * keeps in chain-owned memory lives in one static device array of 65536 ints
+ * (256 KiB) that every GPU using the library holds until the process exits.
+ * A height segment is a maximal run of domain vertices in one row: one per
+ * row for the Aztec diamond, rectangles, hexagons and the domain-wall square,
+ * possibly several per row for non-convex domains from a boundary path;
+ * domains with more than 65536 segments are rejected with TL_EINVAL.  The
+ * array's device address is looked up by tl_ctx_create, once per device.
+ * All calls on a device share the array and each rewrites the entries it
+ * uses, so calls whose work overlaps on the GPU (different streams,
+ * concurrently) race and must be serialised by the caller.  Enqueues on
+ * `stream` only. */
 int tl_read_height_noalloc(tl_chain* c, int32_t* out, size_t cap, void* stream);
 
 /* Edge-occupancy sampling (the densities of Sec. 4's figures).  After this

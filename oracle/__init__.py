@@ -80,6 +80,7 @@ def lib():
             "or_sixv_thresholds": (c.c_int, [dp, u32p]),
             "or_sixv_height": (c.c_int64, [u8p, c.c_int, i32p]),
             "or_accumulate": (None, [u8p, c.c_uint64, u32p]),
+            "or_domino_nsew": (None, [u8p, c.c_int, c.c_int, c.c_int, u32p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -349,6 +350,24 @@ def accumulate(st: np.ndarray, counts: np.ndarray) -> None:
     """Edge-occupancy counters: counts += st (uint32, same shape)."""
     assert counts.dtype == np.uint32 and counts.shape == st.shape
     lib().or_accumulate(_p(st), st.size, _p(counts))
+
+
+def domino_nsew(st: np.ndarray, kappa: int, counts: np.ndarray | None = None) -> np.ndarray:
+    """Per-face domino-type counters (Sec. 4's arctic-circle pictures).
+
+    Adds one to counts[t, y, x] for both squares of every domino, t = 0 north,
+    1 south, 2 east, 3 west, shape [4, H-1, W-1] (uint32).  Horizontal
+    dominoes are north iff the left square's colour (x+y) mod 2 equals kappa,
+    vertical ones west iff the bottom square's colour differs from kappa
+    (kappa = n mod 2 for the Aztec diamond of order n).  Returns counts.
+    """
+    st = np.ascontiguousarray(st, dtype=np.uint8)
+    _, H, W = st.shape
+    if counts is None:
+        counts = np.zeros((4, H - 1, W - 1), dtype=np.uint32)
+    assert counts.dtype == np.uint32 and counts.shape == (4, H - 1, W - 1) and counts.flags["C_CONTIGUOUS"]
+    lib().or_domino_nsew(_p(st), W, H, int(kappa), _p(counts))
+    return counts
 
 
 # --------------------------------------------------------------------------

@@ -409,6 +409,39 @@ OR_EXPORT int64_t or_domino_height(const uint8_t* st, int W, int H, int32_t* h)
     return bad;
 }
 
+/* Domino types for the arctic-circle pictures (Sec. 4).  The paper does   */
+/* not fix the labels; the reading used here: a horizontal domino is north */
+/* iff its left square has colour (x+y) mod 2 == kappa, a vertical domino  */
+/* is west iff its bottom square has colour (x+y) mod 2 != kappa, with     */
+/* kappa = n mod 2 for the Aztec diamond of order n (so the all-horizontal */
+/* start is north in the upper half of the diamond).  Walks the dominoes   */
+/* (crossed edges) and adds one to the type counter of both squares each   */
+/* covers: counts[t][y][x] for faces (x,y), t = 0 N, 1 S, 2 E, 3 W, shape  */
+/* [4][H-1][W-1].                                                           */
+OR_EXPORT void or_domino_nsew(const uint8_t* st, int W, int H, int kappa, uint32_t* counts)
+{
+    size_t nf = (size_t)(W - 1) * (H - 1);
+#define NSEW_ADD(t, fx, fy) counts[(size_t)(t) * nf + (size_t)(fy) * (W - 1) + (fx)] += 1
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            /* Vt(x,y) crossed: horizontal domino on faces (x-1,y), (x,y) */
+            if (DVT(st, W, H, x, y) && x >= 1 && x < W - 1 && y < H - 1) {
+                int left_colour = ((x - 1) + y) & 1;
+                int t = (left_colour == kappa) ? 0 : 1;
+                NSEW_ADD(t, x - 1, y);
+                NSEW_ADD(t, x, y);
+            }
+            /* Hz(x,y) crossed: vertical domino on faces (x,y-1), (x,y) */
+            if (DHZ(st, W, H, x, y) && y >= 1 && y < H - 1 && x < W - 1) {
+                int bottom_colour = (x + (y - 1)) & 1;
+                int t = (bottom_colour != kappa) ? 3 : 2;
+                NSEW_ADD(t, x, y - 1);
+                NSEW_ADD(t, x, y);
+            }
+        }
+#undef NSEW_ADD
+}
+
 /* ======================================================================== */
 /* Lozenge tilings (Sec. 1.2.1)                                             */
 /* ======================================================================== */

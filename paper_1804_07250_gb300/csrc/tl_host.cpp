@@ -96,6 +96,13 @@ TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, cuda_device);
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cuda_device);
     cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, cuda_device);
+    // the allocation-free height call's static scratch: its device address
+    // is looked up here, once per device, so that call itself loads nothing
+    const int e = noalloc_prepare(cuda_device);
+    if (e) {
+        delete c;
+        return fail(TL_ECUDA, "tl_ctx_create: static scratch lookup: %s", cudaGetErrorString((cudaError_t)e));
+    }
     *out = c;
     return TL_OK;
 }
@@ -982,6 +989,21 @@ static bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A caller's buffer in device memory of a GPU other than `device`: the
+// chain's kernels and copies would fault on it (no peer access is set up),
+// so it is rejected with TL_EINVAL.  Host and managed memory pass.
+static int require_local(const void* p, int device, const char* fn)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return TL_OK;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != device)
+        return fail(TL_EINVAL, "%s: the buffer is on device %d, the chain on device %d", fn, a.device, device);
+    return TL_OK;
+}
+
 static cudaStream_t SS(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 template <class T>
@@ -1509,6 +1531,7 @@ TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* s
 {
     if (!c || (!ring && k)) return fail(TL_EINVAL, "tl_run_sweeps_hashed: NULL argument");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (k) TL_TRY(require_local(ring, c->ctx->device, "tl_run_sweeps_hashed"));
     const bool dev = k ? is_device_ptr(ring) : true;
     uint64_t* dring = reinterpret_cast<uint64_t*>(ring);
     uint64_t* tmp = nullptr;
@@ -1553,6 +1576,7 @@ TL_API int tl_read_state(tl_chain* c, uint8_t* canon, size_t cap, void* stream)
     const size_t n = (size_t)c->g.ntype * c->g.W * c->g.H;
     if (cap < n) return fail(TL_EINVAL, "tl_read_state: cap %zu < %zu", cap, n);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(require_local(canon, c->ctx->device, "tl_read_state"));
     if (is_device_ptr(canon)) {
         CUDA_TRY(launch_unpack(c->g, c->rows, canon, stream));
         c->launches += 1;
@@ -1571,6 +1595,7 @@ TL_API int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* str
     const size_t want = (size_t)c->g.ntype * c->g.W * c->g.H;
     if (n != want) return fail(TL_EINVAL, "tl_write_state: n %zu != %zu", n, want);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(require_local(canon, c->ctx->device, "tl_write_state"));
     const bool dev = is_device_ptr(canon);
     std::vector<uint8_t> host;
     const uint8_t* check = canon;
@@ -1590,6 +1615,7 @@ TL_API int tl_state_hash(tl_chain* c, uint64_t* out, void* stream)
 {
     if (!c || !out) return fail(TL_EINVAL, "tl_state_hash: NULL argument");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(require_local(out, c->ctx->device, "tl_state_hash"));
     if (is_device_ptr(out)) {
         CUDA_TRY(launch_hash(c->g, c->rows, reinterpret_cast<unsigned long long*>(out), stream));
         c->launches += 1;
@@ -1652,6 +1678,7 @@ TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_i
     const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W;
     if (cap < ncanon) return fail(TL_EINVAL, "tl_aztec_shuffle: cap %zu < %zu", cap, ncanon);
     CUDA_TRY(cudaSetDevice(ctx->device));
+    TL_TRY(require_local(canon, ctx->device, "tl_aztec_shuffle"));
     std::lock_guard<std::mutex> lock(ctx->shuffle_mu);
     TL_TRY(shuffle_prepare(ctx, n));
     ShuffleCache& sc = ctx->shuffle;
@@ -1753,6 +1780,7 @@ TL_API int tl_read_height(tl_chain* c, int32_t* out, size_t cap, void* stream)
     if (cap < n) return fail(TL_EINVAL, "tl_read_height: cap %zu < %zu", cap, n);
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     int32_t* dst = out;
+    TL_TRY(require_local(out, c->ctx->device, "tl_read_height"));
     const bool dev = is_device_ptr(out);
     if (!dev) {
         if (!c->hscratch) TL_TRY(dev_alloc(&c->hscratch, n, "height scratch"));
@@ -1774,10 +1802,11 @@ TL_API int tl_read_height_noalloc(tl_chain* c, int32_t* out, size_t cap, void* s
     const tl_domain& d = c->dom_copy;
     const size_t n = (size_t)d.hw * d.hh;
     if (cap < n) return fail(TL_EINVAL, "tl_read_height_noalloc: cap %zu < %zu", cap, n);
-    if (d.nseg > noalloc_height_max_rows())
+    if (d.nseg > noalloc_height_max_segments())
         return fail(TL_EINVAL, "tl_read_height_noalloc: %d height segments exceed the static scratch limit of %d",
-                    d.nseg, noalloc_height_max_rows());
+                    d.nseg, noalloc_height_max_segments());
     CUDA_TRY(cudaSetDevice(c->ctx->device));
+    TL_TRY(require_local(out, c->ctx->device, "tl_read_height_noalloc"));
     if (!is_device_ptr(out))
         return fail(TL_EINVAL, "tl_read_height_noalloc: `out` must be device memory (a host buffer would "
                                "need a staging allocation)");
@@ -1805,6 +1834,7 @@ TL_API int tl_density_begin(tl_chain* c, uint32_t stride, uint64_t burn_in)
 template <class F>
 static int to_output(tl_chain* c, double* out, size_t n, void* stream, F launch)
 {
+    TL_TRY(require_local(out, c->ctx->device, "density readback"));
     if (is_device_ptr(out)) {
         const int e = launch(out);
         if (e) return fail(TL_ECUDA, "density kernel: %s", cudaGetErrorString((cudaError_t)e));
@@ -2239,6 +2269,7 @@ TL_API int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream)
     const int e = launch_batch_hash(b->d_chains, b->d_tiles_chain, b->ntiles, b->src, b->d_hash, stream);
     if (e) return fail(TL_ECUDA, "batch hash: %s", cudaGetErrorString((cudaError_t)e));
     b->launches += 1;
+    TL_TRY(require_local(out, b->ctx->device, "tl_batch_hashes"));
     const bool dev = is_device_ptr(out);
     CUDA_TRY(cudaMemcpyAsync(out, b->d_hash, 8 * b->chains.size(), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              SS(stream)));

@@ -89,8 +89,11 @@ int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t*
                             void* stream);
 // Device-generated log-normal weights -> per-site thresholds [H][W].
 int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_t seed, uint32_t* t, void* stream);
-// Height with its segment-offset scratch in a static device array (no allocation).
-int noalloc_height_max_rows();
+// Height with its segment-offset scratch in a static device array (no
+// allocation); noalloc_prepare looks up the array's device address once per
+// device (called when a context is created).
+int noalloc_height_max_segments();
+int noalloc_prepare(int device);
 int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
                           int32_t* out, int device, void* stream);
 

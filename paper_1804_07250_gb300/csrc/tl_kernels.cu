@@ -508,26 +508,30 @@ int launch_lognormal_thresholds(int lattice, int W, int H, double sigma, uint64_
 // under a memory budget that forbids cudaMalloc, or a real-time loop that
 // must not synchronise the device the way cudaMalloc / cudaFree can), the
 // per-segment offsets that launch_height keeps in chain-owned memory live here
-// in one file-scope device array instead.  The array holds kNoAllocMaxRows
-// ints (256 KiB), enough for any box this library accepts (at most 65536
-// rows); every GPU that loads the library keeps it until the process exits.
-// All calls on a device share it: each call rewrites every entry it reads,
-// so nothing needs clearing, but calls whose kernels overlap on the GPU
-// (concurrent streams) race on it and must be serialised by the caller.
+// in one file-scope device array instead.  The array holds kNoAllocMaxSegs
+// ints (256 KiB): one per height segment, a maximal run of domain vertices in
+// one row (one segment per row for the Aztec diamond, rectangles, hexagons and
+// the domain-wall square; a row of a non-convex domain from a boundary path
+// can hold several).  Domains with more segments are rejected.  Every GPU
+// that loads the library keeps the array until the process exits.  All calls
+// on a device share it: each call rewrites every entry it reads, so nothing
+// needs clearing, but calls whose kernels overlap on the GPU (concurrent
+// streams) race on it and must be serialised by the caller.
 // ---------------------------------------------------------------------------
-constexpr int kNoAllocMaxRows = 65536;
-static __device__ __align__(256) int g_noalloc_height_base[kNoAllocMaxRows];
+constexpr int kNoAllocMaxSegs = 65536;
+static __device__ __align__(256) int g_noalloc_height_base[kNoAllocMaxSegs];
 
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static int* g_noalloc_base_dev[kNoAllocMaxDevices];   // device address per device ordinal
 
-int noalloc_height_max_rows() { return kNoAllocMaxRows; }
+int noalloc_height_max_segments() { return kNoAllocMaxSegs; }
 
 // The device address of the scratch array must come from cudaGetSymbolAddress
 // with the device current: in host code the symbol names a host-side stand-in.
-// Done once per device, on the first call made on it.
-static int noalloc_scratch(int device, int** out)
+// Looked up once per device, when a context is created on it (the lookup can
+// load this module, which allocates), so the entry point itself never does.
+int noalloc_prepare(int device)
 {
     if (device < 0 || device >= kNoAllocMaxDevices) return (int)cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -537,14 +541,21 @@ static int noalloc_scratch(int device, int** out)
         if (e != cudaSuccess) return (int)e;
         g_noalloc_base_dev[device] = static_cast<int*>(p);
     }
-    *out = g_noalloc_base_dev[device];
     return 0;
+}
+
+static int noalloc_scratch(int device, int** out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    *out = g_noalloc_base_dev[device];
+    return *out ? 0 : (int)cudaErrorInitializationError;
 }
 
 int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* seg, int nseg, int hw, int hh,
                           int32_t* out, int device, void* stream)
 {
-    if (nseg > kNoAllocMaxRows) return (int)cudaErrorInvalidValue;
+    if (nseg > kNoAllocMaxSegs) return (int)cudaErrorInvalidValue;
     int* base = nullptr;
     const int e = noalloc_scratch(device, &base);
     if (e) return e;

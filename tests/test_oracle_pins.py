@@ -837,3 +837,76 @@ def test_shuffling_is_uniform():
     for seed in range(6400):
         counts[index[O.aztec_shuffle(3, seed).tobytes()]] += 1
     assert _chi2_pvalue(counts, np.full(64, 1 / 64)) > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# North / south / east / west domino types (Sec. 4's arctic-circle pictures)
+# ---------------------------------------------------------------------------
+def _nsew_types(counts):
+    """Face type 0..3 where exactly one counter is set, -1 where none."""
+    tot = counts.sum(0)
+    t = np.where(tot > 0, counts.argmax(0), -1)
+    return tot, t
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 21])
+def test_nsew_all_horizontal_start_is_north_above_south_below(n):
+    # the all-horizontal start: every face in the upper half of the diamond is
+    # covered by a north domino, every face in the lower half by a south one
+    counts = O.domino_nsew(O.aztec(n), n % 2)
+    inside = _aztec_faces(n).astype(bool)
+    tot, t = _nsew_types(counts)
+    assert np.array_equal(tot, inside.astype(np.uint32))
+    ys = np.arange(2 * n)[:, None] * np.ones((1, 2 * n), dtype=int)
+    assert np.all(t[inside & (ys >= n)] == 0)
+    assert np.all(t[inside & (ys < n)] == 1)
+    assert counts[2].sum() == 0 and counts[3].sum() == 0
+
+
+def _rot180(st):
+    # face (x, y) -> (2n-1-x, 2n-1-y); primal edges map Hz(x,y) -> Hz(W-2-x, H-1-y),
+    # Vt(x,y) -> Vt(W-1-x, H-2-y)
+    out = np.zeros_like(st)
+    _, H, W = st.shape
+    out[0, :, : W - 1] = st[0, ::-1, : W - 1][:, ::-1]
+    out[1, : H - 1, :] = st[1, : H - 1, ::-1][::-1, :]
+    return out
+
+
+def _transpose(st):
+    # reflection in the diagonal x <-> y: Hz(x,y) <-> Vt(y,x)
+    return np.ascontiguousarray(np.stack([st[1].T, st[0].T]))
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 30])
+def test_nsew_one_type_per_face_and_symmetries(n):
+    inside = _aztec_faces(n).astype(bool)
+    for seed in range(3):
+        st = O.aztec_shuffle(n, seed, stream=1)
+        counts = O.domino_nsew(st, n % 2)
+        tot, t = _nsew_types(counts)
+        # every face of the diamond carries exactly one type, nothing outside
+        assert np.array_equal(tot, inside.astype(np.uint32))
+        # a half turn keeps colours and swaps north/south and east/west
+        r = _rot180(st)
+        assert O.domino_check(r, inside) == 0
+        cr = O.domino_nsew(r, n % 2)
+        assert np.array_equal(cr[[1, 0, 3, 2]], counts[:, ::-1, ::-1])
+        # the diagonal reflection maps north -> east, south -> west and back
+        tr = _transpose(st)
+        assert O.domino_check(tr, inside) == 0
+        ct = O.domino_nsew(tr, n % 2)
+        assert np.array_equal(ct[[2, 3, 0, 1]], counts.transpose(0, 2, 1))
+
+
+def test_nsew_frozen_corners_carry_the_four_types():
+    # on exact samples of order 30 the four corners of the diamond are frozen:
+    # north brickwork at the top, south at the bottom, west on the left,
+    # east on the right
+    n = 30
+    for seed in range(4):
+        _, t = _nsew_types(O.domino_nsew(O.aztec_shuffle(n, seed, stream=2), n % 2))
+        assert np.all(t[2 * n - 3:, n - 1:n + 1] == 0)       # top: faces (n-1..n, 2n-3..2n-1)
+        assert np.all(t[:3, n - 1:n + 1] == 1)               # bottom
+        assert np.all(t[n - 1:n + 1, 2 * n - 3:] == 2)       # right: east
+        assert np.all(t[n - 1:n + 1, :3] == 3)               # left: west

@@ -68,3 +68,38 @@ def test_noalloc_height_rejects_host_buffers(T):
     with pytest.raises(T.TilingError) as e:
         ch.read_height_noalloc(host)
     assert e.value.code == T.TL_EINVAL
+
+
+def test_noalloc_height_allocates_nothing(T):
+    # after the first call, repeated calls leave the device's free memory
+    # exactly where it was: nothing is allocated, not even lazily
+    import torch
+    ctx = T.Context(0)
+    ch = T.Chain(ctx, T.Domain.aztec(300), seed=3, th=T.thresholds(scalar=1 << 31))
+    ch.run(20)
+    out = torch.empty(ch.domain.height_shape, dtype=torch.int32, device="cuda")
+    ch.read_height_noalloc(out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        ch.read_height_noalloc(out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_height_rejects_too_many_segments(T):
+    # a 6 x 65534 rectangle with a 2 x 4 notch cut from the middle of its top
+    # edge: 65535 vertex rows, four of them split in two by the notch, so
+    # 65539 height segments -- more than the static scratch holds
+    ctx = T.Context(0)
+    steps = ([0] * 6 + [1] * 65534 + [2] * 2 + [3] * 4 + [2] * 2 + [1] * 4 + [2] * 2 + [3] * 65534)
+    dom = T.Domain.from_boundary(T.DOMINO, steps)
+    ch = T.Chain(ctx, dom, seed=1, th=T.thresholds(scalar=1 << 31))
+    import torch
+    out = torch.empty(dom.height_shape, dtype=torch.int32, device="cuda")
+    with pytest.raises(T.TilingError) as e:
+        ch.read_height_noalloc(out)
+    assert e.value.code == T.TL_EINVAL
+    # the allocating call still serves it
+    ref = ch.read_height()
+    assert ref.shape == dom.height_shape
