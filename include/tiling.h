@@ -402,10 +402,15 @@ int tl_read_domino_nsew(tl_chain* c, double* out, size_t cap, void* stream);
  * depend on the plan: the random numbers are keyed by site and sweep.
  *  kernel:            1 one launch per pass over global memory; 2 the
  *                     shared-memory resident multi-sweep kernel (cooperative
- *                     launch; TL_EUNSUPPORTED if the domain does not fit it).
+ *                     launch; TL_EUNSUPPORTED if the domain does not fit it);
+ *                     3 the register-resident multi-sweep kernel for
+ *                     dominoes at t = 2^31 (every 128-site group of a row
+ *                     pair held in one thread's registers; the automatic
+ *                     choice for such chains when it fits, TL_EUNSUPPORTED
+ *                     otherwise).
  *  sweeps_per_launch: cap on sweeps per resident launch.
  *  halo:              passes between boundary exchanges of the resident
- *                     kernel (1..64).
+ *                     kernels (1..64; even for kernel 3).
  *  threads:           threads per CTA of the resident kernel (512 or 1024).
  *  npre:              random bit planes generated ahead per group (1..16).
  * tl_chain_get_plan also fills the resolved values and ctas / smem_bytes. */

@@ -369,7 +369,8 @@ class Chain:
 
     def set_plan(self, kernel: int = 0, sweeps_per_launch: int = 0, halo: int = 0,
                  threads: int = 0, npre: int = 0):
-        """kernel 0 auto / 1 per-pass global / 2 resident; results never depend on it."""
+        """kernel 0 auto / 1 per-pass global / 2 shared-memory resident / 3
+        register-resident (dominoes at t = 2^31); results never depend on it."""
         p = Plan(kernel, sweeps_per_launch, halo, threads, npre, 0, 0)
         _check(_lib.tl_chain_set_plan(self._h, ctypes.byref(p)))
 

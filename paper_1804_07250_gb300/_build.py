@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtiling.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tl_kernels.cu", "tl_resident.cu", "tl_batch.cu", "tl_shuffle.cu", "tl_host.cpp", "tl_thurston.cpp"]
+SOURCES = ["tl_kernels.cu", "tl_resident.cu", "tl_regdom.cu", "tl_batch.cu", "tl_shuffle.cu", "tl_host.cpp", "tl_thurston.cpp"]
 
 
 def nvcc() -> str:

@@ -956,6 +956,10 @@ struct tl_chain {
     size_t colours_cap = 0;
     unsigned int epoch = 0;
     std::string res_why;
+    // register-resident domino kernel (dominoes at t = 2^31)
+    bool use_reg = false;
+    RegPlan reg{};
+    int2* hull_d = nullptr;
 };
 
 static void chain_free(tl_chain* c)
@@ -976,6 +980,7 @@ static void chain_free(tl_chain* c)
     cudaFree(c->stripe_d);
     cudaFree(c->xbuf_d);
     cudaFree(c->status_d);
+    cudaFree(c->hull_d);
     delete c;
 }
 
@@ -1168,28 +1173,33 @@ static bool want_resident(tl_chain* c);
 
 TL_API int tl_chain_set_plan(tl_chain* c, const tl_plan* p)
 {
-    if (!c || !p || p->kernel < 0 || p->kernel > 2 || p->sweeps_per_launch < 0 || p->halo < 0 ||
+    if (!c || !p || p->kernel < 0 || p->kernel > 3 || p->sweeps_per_launch < 0 || p->halo < 0 ||
         p->halo > 64 || (p->threads != 0 && p->threads != 512 && p->threads != 1024) || p->npre < 0 ||
         p->npre > 16)
         return fail(TL_EINVAL, "tl_chain_set_plan: bad plan");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
-    c->kernel = p->kernel;
+    const bool kernel_changed = (p->kernel >= 2) != (c->kernel >= 2) || (c->kernel >= 2 && p->kernel != c->kernel);
     c->spl = p->sweeps_per_launch;
-    if (p->halo != c->halo_req || p->threads != c->threads_req || p->npre != c->npre_req) {
+    if (p->halo != c->halo_req || p->threads != c->threads_req || p->npre != c->npre_req || kernel_changed) {
         CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(c->stripe_d);
         cudaFree(c->xbuf_d);
         cudaFree(c->status_d);
+        cudaFree(c->hull_d);
         c->stripe_d = nullptr;
         c->xbuf_d = nullptr;
         c->status_d = nullptr;
+        c->hull_d = nullptr;
+        c->use_reg = false;
         c->res_ready = c->res_failed = false;
         c->halo_req = p->halo;
         c->threads_req = p->threads;
         c->npre_req = p->npre;
     }
-    if (p->kernel == 2 && !want_resident(c))
-        return fail(TL_EUNSUPPORTED, "resident kernel unavailable: %s", c->res_why.c_str());
+    c->kernel = p->kernel;
+    if (p->kernel >= 2 && (!want_resident(c) || (p->kernel == 3) != c->use_reg))
+        return fail(TL_EUNSUPPORTED, "%s kernel unavailable: %s", p->kernel == 3 ? "register-resident" : "resident",
+                    c->res_why.c_str());
     return TL_OK;
 }
 
@@ -1198,7 +1208,7 @@ TL_API int tl_chain_get_plan(tl_chain* c, tl_plan* p)
     if (!c || !p) return fail(TL_EINVAL, "tl_chain_get_plan: NULL argument");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     const bool res = want_resident(c);
-    p->kernel = res ? 2 : 1;
+    p->kernel = res ? (c->use_reg ? 3 : 2) : 1;
     p->sweeps_per_launch = c->spl;
     p->halo = res ? c->res.halo : 0;
     p->threads = res ? c->res.threads : 256;
@@ -1310,9 +1320,194 @@ static void stripe_local(int lo, int hi, int k, int C, int h, int H, int* slo, i
     *shi = k == C - 1 ? H + 1 : hi + h;
 }
 
+// Register-resident domino kernel: the groups each row pair holds, a stripe
+// partition of the pairs that balances the work of a cycle (owned pairs every
+// pass, halo pairs while they can still reach the stripe), and buffers.
+static int plan_regdom(tl_chain* c)
+{
+    const Geom& g = c->g;
+    const tl_domain& d = c->dom_copy;
+    const int h = c->halo_req > 0 ? c->halo_req : 8;
+    if (h & 1) {
+        c->res_why = "the register-resident kernel needs an even halo";
+        return TL_EUNSUPPORTED;
+    }
+    const int H = g.H, W = g.W;
+    const int npairs = (H + 1) / 2;
+    const int hp = h / 2;
+    // extents of the domain's faces per face row
+    std::vector<int> fmin(std::max(H - 1, 0), 1 << 30), fmax(std::max(H - 1, 0), -1);
+    for (int fy = 0; fy + 1 < H; ++fy)
+        for (int fx = 0; fx + 1 < W; ++fx)
+            if (d.cover[(size_t)fy * (W - 1) + fx]) {
+                fmin[fy] = std::min(fmin[fy], fx);
+                fmax[fy] = std::max(fmax[fy], fx);
+            }
+    auto join = [](int2 a, int2 b) {
+        if (a.y <= a.x) return b;
+        if (b.y <= b.x) return a;
+        return make_int2(std::min(a.x, b.x), std::max(a.y, b.y));
+    };
+    // groups of row y holding sites or edges of domain faces (Hz(x,y) lies
+    // between faces (x,y-1) and (x,y), Vt(x,y) between (x-1,y) and (x,y))
+    auto row_groups = [&](int y) {
+        if (y < 0 || y >= H) return make_int2(0, 0);
+        int2 r = d.grange[y];
+        for (int fy = y - 1; fy <= y; ++fy) {
+            if (fy < 0 || fy + 1 >= H || fmax[fy] < 0) continue;
+            r = join(r, make_int2(fmin[fy] >> 8, ((fmax[fy] + 1) >> 8) + 1));
+        }
+        return r;
+    };
+    std::vector<int2> hull(npairs);
+    std::vector<long> w(npairs), pre(npairs + 1, 0);
+    for (int q = 0; q < npairs; ++q) {
+        int2 r = join(row_groups(2 * q), row_groups(2 * q + 1));
+        if (2 * q + 2 < H) r = join(r, d.grange[2 * q + 2]);
+        hull[q] = r.y > r.x ? r : make_int2(0, 0);
+        w[q] = hull[q].y - hull[q].x;
+        pre[q + 1] = pre[q] + w[q];
+    }
+    const int max_threads = 512;
+    auto items = [&](int a, int b) {
+        const int lo = a > 0 ? std::max(0, a - hp) : a, hi = b < npairs ? std::min(npairs, b + hp) : b;
+        return pre[hi] - pre[lo];
+    };
+    auto cost = [&](int a, int b) {
+        long v = (long)h * (pre[b] - pre[a]);
+        for (int k = 1; k <= hp; ++k) {
+            if (a > 0 && a - k >= 0) v += w[a - k] * (h - (2 * k - 1));
+            if (b < npairs && b + k - 1 < npairs) v += w[b + k - 1] * (h - (2 * k - 2));
+        }
+        return v;
+    };
+    // greedy stripes under a cost bound; bounds empty if infeasible
+    auto partition = [&](long T, std::vector<int>& lo) {
+        lo.assign(1, 0);
+        int a = 0;
+        while (a < npairs) {
+            int b = std::min(npairs, a + hp);
+            if (cost(a, b) > T || items(a, b) > max_threads) return false;
+            while (b < npairs && cost(a, b + 1) <= T && items(a, b + 1) <= max_threads) ++b;
+            if (b < npairs && npairs - b < hp) {
+                b = npairs - hp;
+                if (b - a < hp) return false;
+            }
+            lo.push_back(b);
+            a = b;
+            if ((int)lo.size() - 1 > c->ctx->sms) return false;
+        }
+        return true;
+    };
+    if (npairs < 2 * hp) {
+        c->res_why = "domain too small for register-resident stripes";
+        return TL_EUNSUPPORTED;
+    }
+    std::vector<int> best;
+    long tlo = 0, thi = cost(0, npairs) + 1;
+    {
+        std::vector<int> tmp;
+        if (!partition(thi, tmp)) {
+            // even one stripe per SM does not fit the thread limit at any bound
+            long big = 1L << 60;
+            if (!partition(big, tmp)) {
+                c->res_why = "a stripe holds more groups than the register-resident kernel takes";
+                return TL_EUNSUPPORTED;
+            }
+            thi = big;
+        }
+        best = tmp;
+    }
+    while (tlo + 1 < thi) {
+        const long mid = tlo + (thi - tlo) / 2;
+        std::vector<int> tmp;
+        if (partition(mid, tmp)) {
+            thi = mid;
+            best = tmp;
+        } else {
+            tlo = mid;
+        }
+    }
+    const int C = (int)best.size() - 1;
+    int max_items = 0, max_npl = 0;
+    for (int k = 0; k < C; ++k) {
+        max_items = std::max(max_items, (int)items(best[k], best[k + 1]));
+        const int plo = k > 0 ? best[k] - hp : best[k], phi = k < C - 1 ? best[k + 1] + hp : best[k + 1];
+        max_npl = std::max(max_npl, phi - plo);
+    }
+    const int threads = std::max(32, (max_items + 31) / 32 * 32);
+    size_t smem = regdom_smem_bytes(threads, max_npl);
+    // one CTA per SM: ask for more than half of an SM's shared memory
+    smem = std::max(smem, (size_t)c->ctx->smem_optin / 2 + 1024);
+    if ((long)smem > (long)c->ctx->smem_optin) {
+        c->res_why = "register-resident tables do not fit in shared memory";
+        return TL_EUNSUPPORTED;
+    }
+    int bps = 0;
+    if (regdom_prepare(threads, smem, &bps) != 0 || bps < 1) {
+        c->res_why = "register-resident kernel does not fit on an SM";
+        return TL_EUNSUPPORTED;
+    }
+    if (C > bps * c->ctx->sms) {
+        c->res_why = "too many stripes for a cooperative launch";
+        return TL_EUNSUPPORTED;
+    }
+    std::vector<int> rows_lo(C + 1);
+    for (int k = 0; k <= C; ++k) rows_lo[k] = 2 * best[k];
+    int rc;
+    if ((rc = dev_alloc(&c->stripe_d, (size_t)C + 1, "stripes")) ||
+        (rc = dev_alloc(&c->hull_d, (size_t)npairs, "pair hulls")) ||
+        (rc = dev_alloc(&c->xbuf_d, (size_t)C * 4 * h * g.row_words, "exchange buffer")) ||
+        (rc = dev_alloc(&c->status_d, 1, "status")))
+        return rc;
+    CUDA_TRY(cudaMemcpy(c->stripe_d, rows_lo.data(), sizeof(int) * (C + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->hull_d, hull.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(c->xbuf_d, 0, sizeof(unsigned long long) * C * 4 * h * g.row_words));
+    CUDA_TRY(cudaMemset(c->status_d, 0, sizeof(int)));
+    c->reg.ctas = C;
+    c->reg.threads = threads;
+    c->reg.halo = h;
+    c->reg.smem_bytes = smem;
+    c->reg.stripe_lo = c->stripe_d;
+    c->reg.hull = c->hull_d;
+    c->reg.xbuf = c->xbuf_d;
+    c->reg.status = c->status_d;
+    // the common fields, for reporting and the launch loop
+    c->res = ResidentPlan{};
+    c->res.ctas = C;
+    c->res.threads = threads;
+    c->res.halo = h;
+    c->res.npre = 1;
+    c->res.fast = true;
+    c->res.smem_bytes = smem;
+    c->res.stripe_lo = c->stripe_d;
+    c->res.xbuf = c->xbuf_d;
+    c->res.status = c->status_d;
+    c->use_reg = true;
+    c->res_ready = true;
+    return TL_OK;
+}
+
 // Stripe partition, shared-memory budget and buffers of the resident kernel.
 static int plan_resident(tl_chain* c)
 {
+    if (c->kernel != 2 && fast_candidate(c) && c->g.Kg <= 4096) {
+        const int rc = plan_regdom(c);
+        if (rc == TL_OK) return TL_OK;
+        if (c->kernel == 3) return rc;
+        cudaFree(c->stripe_d);
+        cudaFree(c->hull_d);
+        cudaFree(c->xbuf_d);
+        cudaFree(c->status_d);
+        c->stripe_d = nullptr;
+        c->hull_d = nullptr;
+        c->xbuf_d = nullptr;
+        c->status_d = nullptr;
+    }
+    if (c->kernel == 3) {
+        c->res_why = "the register-resident kernel covers dominoes at t = 2^31 only";
+        return TL_EUNSUPPORTED;
+    }
     const Geom& g = c->g;
     const tl_domain& d = c->dom_copy;
     const int h = c->halo_req > 0 ? c->halo_req : default_halo(c);
@@ -1463,9 +1658,14 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
             if (ec) return fail(TL_ECUDA, "colour kernel: %s", cudaGetErrorString((cudaError_t)ec));
             c->launches += 1;
         }
-        const int e = launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th,
-                                      c->grange, ++c->epoch, ring ? ring + done : nullptr,
-                                      dens ? c->cplanes : nullptr, c->burn, dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
+        const int e =
+            c->use_reg
+                ? launch_regdom(c->g, c->rows, c->reg, (uint32_t)c->sweep, (uint32_t)n, c->rng, ++c->epoch,
+                                ring ? ring + done : nullptr, dens ? c->cplanes : nullptr, c->burn,
+                                dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream)
+                : launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th, c->grange,
+                                  ++c->epoch, ring ? ring + done : nullptr, dens ? c->cplanes : nullptr, c->burn,
+                                  dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
         if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
         if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
         c->sweep += n;

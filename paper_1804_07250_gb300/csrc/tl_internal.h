@@ -132,6 +132,27 @@ int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uin
 // Colours of the pass slots of nsweeps sweeps under the random pass order.
 int launch_slot_colours(uint8_t* out, uint32_t sweep0, uint32_t nsweeps, int passes, const DevRng& rng, void* stream);
 
+// Register-resident domino kernel at t = 2^31 (tl_regdom.cu).  Stripes of
+// whole row pairs (2q, 2q + 1); pair q holds groups [hull[q].x, hull[q].y)
+// (every group where its rows have sites or edges of domain faces, or the
+// row above has sites); one thread per held group of the stripe and of
+// `halo` rows on each side.
+struct RegPlan {
+    int ctas;
+    int threads;                   // threads per CTA (<= 512, multiple of 32)
+    int halo;                      // even
+    size_t smem_bytes;
+    const int* stripe_lo;          // device [ctas + 1], even
+    const int2* hull;              // device [pairs]
+    unsigned long long* xbuf;      // device [ctas][2][2][halo / 2][16][Kg][2]
+    int* status;
+};
+size_t regdom_smem_bytes(int threads, int max_local_pairs);
+int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm);
+int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t sweep0, uint32_t nsweeps,
+                  const DevRng& rng, unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
+                  uint32_t stride, const uint8_t* colours, void* stream);
+
 // ---- batched chains (tl_batch.cu) ----
 struct BatchChain {
     Geom g;

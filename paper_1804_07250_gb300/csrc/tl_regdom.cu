@@ -1,0 +1,499 @@
+// Register-resident multi-sweep kernel for domino tilings at t = 2^31
+// (cooperative launch, one CTA per SM).
+//
+// The paper moves the whole tiling through device memory twice per
+// half-step (Rotate, then Update; Sec. 2.2).  Here every thread owns one
+// 128-site group of two consecutive vertex rows -- 32 state words (edges Hz
+// and Vt of both x parities, four words each per row) plus a copy of the Vt
+// words of the row below -- and keeps them in registers for the whole
+// launch.  A pass updates every site of one colour class (x + y mod 2,
+// Sec. 1.1.3): each row of the pair has one parity per pass, so the update
+// is straight-line bit logic on registers; the heat-bath decision at
+// t = 2^31 needs only the first random plane of Philox4x32-10 (bit 31 of
+// u < 2^31 iff that bit is 0).
+//
+// A site reads the four edges around it.  Two of them can belong to another
+// thread: the W edge of a group's first site (top bit of the neighbouring
+// group's odd-Hz word) and the Vt edges shared with the row pairs above and
+// below.  After the pass every thread publishes what it flipped that others
+// hold (its rows' flip masks, and the two boundary bits), one CTA barrier
+// later every thread applies its neighbours' flips.  One barrier per pass;
+// shared memory carries 36 bytes per thread and pass.
+//
+// Between CTAs the stripes exchange boundary rows every `halo` passes (the
+// halo rows are recomputed redundantly, the exact region shrinking by one
+// row per pass; rows whose results can no longer reach the owned stripe are
+// skipped).  Boundary words travel as 64-bit words tagged with (launch
+// epoch, cycle), double buffered by cycle parity; every wait is bounded
+// (2 s) and raises a status word instead of hanging.
+#include "tl_device.cuh"
+
+#include <cstdint>
+
+namespace tl {
+
+struct RegParams {
+    uint32_t* rows0;            // global row 0 (after the pad row)
+    Geom g;
+    const int* stripe_lo;       // [C + 1] even row bounds
+    const int2* hull;           // [pairs] groups [x, y) held for rows (2q, 2q + 1)
+    int halo;                   // rows per side = passes per exchange cycle (even)
+    const uint8_t* colours;     // random pass order: colour of every slot, else nullptr
+    uint32_t sweep0, nsweeps;
+    DevRng rng;
+    unsigned long long* xbuf;   // [C][2][2][halo / 2][16][Kg][2] tagged words
+    int* status;
+    unsigned long long* ring;
+    uint32_t* counts;
+    uint64_t burn;
+    uint32_t stride;
+    unsigned int epoch;
+};
+
+TL_DEV uint64_t rd_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+TL_DEV void rd_ld2(const unsigned long long* p, unsigned long long* a, unsigned long long* b)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(*a), "=l"(*b) : "l"(p) : "memory");
+}
+TL_DEV void rd_st2(unsigned long long* p, unsigned long long a, unsigned long long b)
+{
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+constexpr uint64_t kRegWaitLimitNs = 2000000000ull;   // 2 s: far beyond any healthy exchange
+
+// One row at parity 0 (sites x = 2j): E = Hz(2j) (even plane), W = Hz(2j-1)
+// (odd plane shifted up by one site; bit 0 from `pv`, the top bit of the
+// left group's odd word), N = Vt(2j, y), S = Vt(2j, y-1).  Returns the flip
+// mask and applies it to the row's own words; `lb` receives bit 0 of the
+// mask (the flip of the left group's odd-Hz top bit).
+TL_DEV uint4 row_par0(uint4& He, uint4& Ho, uint32_t& pv, uint4& N, uint4& S, uint4 o, uint32_t& lb)
+{
+    const uint4 Wd = shl1(Ho, pv);
+    uint4 fl;
+#define TL_RG_F(c)                                                                                  \
+    {                                                                                               \
+        const uint32_t f = (He.c & Wd.c & ~(N.c | S.c)) | (N.c & S.c & ~(He.c | Wd.c));           \
+        fl.c = f & (~o.c ^ He.c);                                                                   \
+    }
+    TL_RG_F(x) TL_RG_F(y) TL_RG_F(z) TL_RG_F(w)
+#undef TL_RG_F
+    He = x4(He, fl);
+    N = x4(N, fl);
+    S = x4(S, fl);
+    Ho.x ^= (fl.x >> 1) | (fl.y << 31);
+    Ho.y ^= (fl.y >> 1) | (fl.z << 31);
+    Ho.z ^= (fl.z >> 1) | (fl.w << 31);
+    Ho.w ^= fl.w >> 1;
+    pv ^= fl.x << 31;
+    lb = fl.x & 1u;
+    return fl;
+}
+
+// One row at parity 1 (sites x = 2j + 1): E = Hz(2j+1) (odd plane), W =
+// Hz(2j) (even plane), N = Vt(2j+1, y), S = Vt(2j+1, y-1).  `rb` receives the
+// top bit of the mask (the last site's E edge is the right group's `pv`).
+TL_DEV uint4 row_par1(uint4& He, uint4& Ho, uint4& N, uint4& S, uint4 o, uint32_t& rb)
+{
+    uint4 fl;
+#define TL_RG_F(c)                                                                                  \
+    {                                                                                               \
+        const uint32_t f = (Ho.c & He.c & ~(N.c | S.c)) | (N.c & S.c & ~(Ho.c | He.c));           \
+        fl.c = f & (~o.c ^ Ho.c);                                                                   \
+    }
+    TL_RG_F(x) TL_RG_F(y) TL_RG_F(z) TL_RG_F(w)
+#undef TL_RG_F
+    He = x4(He, fl);
+    Ho = x4(Ho, fl);
+    N = x4(N, fl);
+    S = x4(S, fl);
+    rb = fl.w >> 31;
+    return fl;
+}
+
+// The 32 words of a pair as the exchange sends them: row y0 then row y0 + 1,
+// each He, Ho, Ve, Vo.
+struct PairWords {
+    uint4 v[8];
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
+{
+    extern __shared__ uint4 rsm[];
+    __shared__ int s_ok;
+    __shared__ unsigned long long s_red[NT / 32];
+    const int nt = blockDim.x;
+    uint4* FL0 = rsm;                                        // [2][nt] flips of row y0 (for the pair below)
+    uint4* FL1 = FL0 + 2 * nt;                               // [2][nt] flips of row y0+1 (for the pair above)
+    uint4* RV = FL1 + 2 * nt;                                // [nt][2] Vt words of row y0+1 (refresh)
+    uint2* RH = reinterpret_cast<uint2*>(RV + 2 * nt);       // [nt] odd-Hz top words (refresh)
+    uint32_t* HB = reinterpret_cast<uint32_t*>(RH + nt);     // [2][nt] boundary flip bits
+    int* s_off = reinterpret_cast<int*>(HB + 2 * nt);        // [npl + 1] item offsets of the local pairs
+    const Geom& g = P.g;
+    const int K = g.K, Kg = g.Kg;
+    const int64_t RW = g.row_words;
+    const int c = blockIdx.x, C = gridDim.x, tid = threadIdx.x;
+    const int lo = P.stripe_lo[c], hi = P.stripe_lo[c + 1];
+    const bool bot = (c == 0), top = (c == C - 1);
+    const int h = P.halo;
+    const int slo = bot ? lo : lo - h;
+    const int shi = top ? hi : hi + h;
+    const int q0 = slo >> 1, npl = (shi - slo) >> 1;
+    int2* s_hull = reinterpret_cast<int2*>((reinterpret_cast<uintptr_t>(s_off + npl + 1) + 7) & ~(uintptr_t)7);
+
+    for (int i = tid; i < npl; i += nt) s_hull[i] = P.hull[q0 + i];
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int i = 0; i < npl; ++i) {
+            s_off[i] = run;
+            const int2 hh = s_hull[i];
+            run += hh.y > hh.x ? hh.y - hh.x : 0;
+        }
+        s_off[npl] = run;
+    }
+    __syncthreads();
+    const int nitems = s_off[npl];
+    const bool act = tid < nitems;
+
+    // ---- my item: pair index, group, neighbours, role ----
+    int pi = 0, m = 0, ib = -1, ia = -1, il = -1, ir = -1;
+    if (act) {
+        int a = 0, b = npl - 1;
+        while (a < b) {   // last pair whose first item is <= tid
+            const int mid = (a + b + 1) >> 1;
+            if (s_off[mid] <= tid) a = mid;
+            else b = mid - 1;
+        }
+        pi = a;
+        const int2 hh = s_hull[pi];
+        m = hh.x + (tid - s_off[pi]);
+        if (m > hh.x) il = tid - 1;
+        if (m + 1 < hh.y) ir = tid + 1;
+        if (pi > 0) {
+            const int2 hb = s_hull[pi - 1];
+            if (m >= hb.x && m < hb.y) ib = s_off[pi - 1] + (m - hb.x);
+        }
+        if (pi + 1 < npl) {
+            const int2 ha = s_hull[pi + 1];
+            if (m >= ha.x && m < ha.y) ia = s_off[pi + 1] + (m - ha.x);
+        }
+    }
+    const int y0 = slo + 2 * pi;
+    const bool owned = act && y0 >= lo && y0 < hi;
+    // Halo pairs are updated in pass i of a cycle while dist + i <= halo.  A
+    // row's flips change its own edges and the Vt edges of the row below, so
+    // a row at distance e from the stripe is needed after pass i while
+    // e + i <= halo (below the stripe: dist = e of the pair's upper row,
+    // 1, 3, 5, ...), and above the stripe its flips are also needed while
+    // the row below it is (dist = e - 1 of the pair's lower row, 0, 2, ...).
+    const int dist = owned ? 0 : (y0 < lo ? lo - (y0 + 1) : y0 - hi);
+
+    // ---- load the state ----
+    uint4 He0 = {}, Ho0 = {}, Ve0 = {}, Vo0 = {}, He1 = {}, Ho1 = {}, Ve1 = {}, Vo1 = {}, Se = {}, So = {};
+    uint32_t pv0 = 0, pv1 = 0;
+    const int k0 = 4 * m;
+    if (act) {
+        const uint32_t* b0 = P.rows0 + (int64_t)y0 * RW + k0;
+        const uint32_t* b1 = b0 + RW;
+        const uint32_t* bs = b0 - RW;
+        He0 = __ldcg(reinterpret_cast<const uint4*>(b0));
+        Ho0 = __ldcg(reinterpret_cast<const uint4*>(b0 + K));
+        Ve0 = __ldcg(reinterpret_cast<const uint4*>(b0 + 2 * K));
+        Vo0 = __ldcg(reinterpret_cast<const uint4*>(b0 + 3 * K));
+        He1 = __ldcg(reinterpret_cast<const uint4*>(b1));
+        Ho1 = __ldcg(reinterpret_cast<const uint4*>(b1 + K));
+        Ve1 = __ldcg(reinterpret_cast<const uint4*>(b1 + 2 * K));
+        Vo1 = __ldcg(reinterpret_cast<const uint4*>(b1 + 3 * K));
+        Se = __ldcg(reinterpret_cast<const uint4*>(bs + 2 * K));
+        So = __ldcg(reinterpret_cast<const uint4*>(bs + 3 * K));
+        if (m > 0) {
+            pv0 = __ldcg(b0 + K - 1);
+            pv1 = __ldcg(b1 + K - 1);
+        }
+    }
+    const uint32_t grp0 = (uint32_t)y0 * (uint32_t)Kg + (uint32_t)m;
+    const uint32_t grp1 = grp0 + (uint32_t)Kg;
+
+    const uint64_t total = (uint64_t)P.nsweeps * 2;
+    const size_t side_words = (size_t)(h >> 1) * 32 * Kg;   // u64 per side
+    uint64_t done = 0;
+    int cyc = 0, buf = 0;
+    uint32_t sweep = P.sweep0, slot = 0;
+    // random words of the next pass, computed before the barrier of the
+    // current one (they depend on no state)
+    uint4 o0 = {}, o1 = {};
+    if (act) {
+        o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+        o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+    }
+    while (true) {
+        const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
+        for (int ip = 1; ip <= hc; ++ip) {
+            const uint32_t col = P.colours ? (uint32_t)P.colours[(size_t)(sweep - P.sweep0) * 2 + slot] : slot;
+            const bool par1 = (col & 1u) != 0;   // parity of row y0 (y0 is even)
+            const bool live = act && (dist + ip <= h);
+            // the next pass slot
+            const uint32_t nslot = slot ^ 1u, nsweep = slot ? sweep + 1 : sweep;
+            if (live) {
+                uint4 f0, f1;
+                uint32_t b0, b1;
+                if (!par1) {
+                    f0 = row_par0(He0, Ho0, pv0, Ve0, Se, o0, b0);
+                    f1 = row_par1(He1, Ho1, Vo1, Vo0, o1, b1);
+                } else {
+                    f0 = row_par1(He0, Ho0, Vo0, So, o0, b0);
+                    f1 = row_par0(He1, Ho1, pv1, Ve1, Ve0, o1, b1);
+                }
+                FL0[buf * nt + tid] = f0;
+                FL1[buf * nt + tid] = f1;
+                HB[buf * nt + tid] = b0 | (b1 << 1);
+                if (ip < hc || done + hc < total) {
+                    o0 = philox10(grp0, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
+                    o1 = philox10(grp1, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
+                }
+            }
+            __syncthreads();
+            if (live) {
+                // the pair below flipped its upper row (Vt row y0-1 at the
+                // other parity); the pair above its lower row (Vt row y0+1 at
+                // this parity); left / right groups their boundary bits
+                const uint4 zb = make_uint4(0u, 0u, 0u, 0u);
+                const uint4 fb = ib >= 0 ? FL1[buf * nt + ib] : zb;
+                const uint4 fa = ia >= 0 ? FL0[buf * nt + ia] : zb;
+                const uint32_t hl = il >= 0 ? HB[buf * nt + il] : 0u;
+                const uint32_t hr = ir >= 0 ? HB[buf * nt + ir] : 0u;
+                if (!par1) {
+                    So = x4(So, fb);
+                    Ve1 = x4(Ve1, fa);
+                    Ho0.w ^= (hr & 1u) << 31;          // right group's first site, row y0
+                    pv1 ^= ((hl >> 1) & 1u) << 31;     // left group's last site, row y0+1
+                } else {
+                    Se = x4(Se, fb);
+                    Vo1 = x4(Vo1, fa);
+                    pv0 ^= (hl & 1u) << 31;            // left group's last site, row y0
+                    Ho1.w ^= ((hr >> 1) & 1u) << 31;   // right group's first site, row y0+1
+                }
+            }
+            buf ^= 1;
+            if (slot == 1u) {
+                // end of a sweep: owned rows are exact
+                const uint64_t ndone = (uint64_t)sweep + 1;
+                const bool sample = P.counts && P.stride && ndone >= P.burn && (ndone - P.burn) % P.stride == 0;
+                if (P.ring || sample) {
+                    uint64_t acc = 0;
+                    if (owned) {
+                        const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int y = y0 + r;
+                            if (y >= g.H) continue;
+#pragma unroll
+                            for (int pl = 0; pl < 4; ++pl) {
+                                const uint4 v4 = pw.v[4 * r + pl];
+                                const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) {
+                                    const uint32_t v = vv[w];
+                                    if (!v) continue;
+                                    if (P.ring) acc += word_hash(v, g, y, pl, k0 + w);
+                                    if (sample)
+                                        word_count_sliced(v, (int64_t)y * RW + (int64_t)pl * K + k0 + w,
+                                                          (int64_t)g.H * RW, P.counts);
+                                }
+                            }
+                        }
+                    }
+                    if (P.ring) {
+                        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+                        if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+                        __syncthreads();
+                        if (tid == 0) {
+                            unsigned long long t = 0;
+                            for (int wv = 0; wv < (nt + 31) / 32; ++wv) t += s_red[wv];
+                            atomicAdd(P.ring + (sweep - P.sweep0), t);
+                        }
+                    }
+                }
+            }
+            sweep = nsweep;
+            slot = nslot;
+        }
+        done += (uint64_t)hc;
+        if (done >= total) break;
+
+        // ---- exchange of boundary rows with the neighbouring stripes ----
+        const int par = cyc & 1;
+        const unsigned long long tag =
+            ((unsigned long long)(((P.epoch & 0xFFFFu) << 16) | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
+        if (owned) {
+            const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+            for (int s = 0; s < 2; ++s) {
+                const bool pub = s == 0 ? (!bot && y0 < lo + h) : (!top && y0 >= hi - h);
+                if (!pub) continue;
+                const int idx = s == 0 ? (y0 - lo) >> 1 : (y0 - (hi - h)) >> 1;
+                unsigned long long* dst = P.xbuf + ((size_t)(c * 2 + par) * 2 + s) * side_words +
+                                          (size_t)idx * 32 * Kg;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {   // 16-byte unit u: words 2u, 2u + 1 of the pair
+                    const uint4 v = pw.v[u >> 1];
+                    const uint32_t a = (u & 1) ? v.z : v.x, b = (u & 1) ? v.w : v.y;
+                    rd_st2(dst + ((size_t)u * Kg + m) * 2, tag | a, tag | b);
+                }
+            }
+        }
+        int ok = 1;
+        if (act && !owned) {
+            // halo pair: poll the neighbour's published words, one row at a time
+            const bool below = y0 < lo;
+            const int idx = below ? (y0 - (lo - h)) >> 1 : (y0 - hi) >> 1;
+            const unsigned long long* src = P.xbuf +
+                                            ((size_t)((below ? c - 1 : c + 1) * 2 + par) * 2 + (below ? 1 : 0)) *
+                                                side_words +
+                                            (size_t)idx * 32 * Kg;
+            const uint64_t t_wait = rd_globaltimer();
+            PairWords pw;
+#pragma unroll
+            for (int r = 0; r < 2 && ok; ++r) {
+                unsigned long long a[8], b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) rd_ld2(src + ((size_t)(8 * r + q) * Kg + m) * 2, &a[q], &b[q]);
+                unsigned need = 0xFFu;
+                while (true) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if ((need >> q & 1u) && (a[q] & 0xFFFFFFFF00000000ull) == tag &&
+                            (b[q] & 0xFFFFFFFF00000000ull) == tag)
+                            need &= ~(1u << q);
+                    if (!need) break;
+                    if (*(volatile int*)P.status || rd_globaltimer() - t_wait > kRegWaitLimitNs) {
+                        atomicExch(P.status, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (need >> q & 1u) rd_ld2(src + ((size_t)(8 * r + q) * Kg + m) * 2, &a[q], &b[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    pw.v[4 * r + q] = make_uint4((uint32_t)a[2 * q], (uint32_t)b[2 * q], (uint32_t)a[2 * q + 1],
+                                                 (uint32_t)b[2 * q + 1]);
+            }
+            if (ok) {
+                He0 = pw.v[0]; Ho0 = pw.v[1]; Ve0 = pw.v[2]; Vo0 = pw.v[3];
+                He1 = pw.v[4]; Ho1 = pw.v[5]; Ve1 = pw.v[6]; Vo1 = pw.v[7];
+            }
+        }
+        // copies of the row below (Vt) and of the left group's odd-Hz top
+        // words from the neighbouring items, now exact again
+        if (act) {
+            RV[2 * tid] = Ve1;
+            RV[2 * tid + 1] = Vo1;
+            RH[tid] = make_uint2(Ho0.w, Ho1.w);
+        }
+        if (tid == 0) s_ok = 1;
+        __syncthreads();
+        if (!ok) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) return;   // the state is undefined; the host reports TL_ETIMEOUT
+        if (act) {
+            if (ib >= 0) {
+                Se = RV[2 * ib];
+                So = RV[2 * ib + 1];
+            }
+            if (il >= 0) {
+                const uint2 r = RH[il];
+                pv0 = r.x;
+                pv1 = r.y;
+            }
+            if (!owned) {
+                // halo items skipped the end of the cycle: their next random
+                // words were not drawn
+                o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+                o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+            }
+        }
+        ++cyc;
+    }
+    if (owned) {
+        uint32_t* b0 = P.rows0 + (int64_t)y0 * RW + k0;
+        __stcg(reinterpret_cast<uint4*>(b0), He0);
+        __stcg(reinterpret_cast<uint4*>(b0 + K), Ho0);
+        __stcg(reinterpret_cast<uint4*>(b0 + 2 * K), Ve0);
+        __stcg(reinterpret_cast<uint4*>(b0 + 3 * K), Vo0);
+        if (y0 + 1 < g.H) {
+            uint32_t* b1 = b0 + RW;
+            __stcg(reinterpret_cast<uint4*>(b1), He1);
+            __stcg(reinterpret_cast<uint4*>(b1 + K), Ho1);
+            __stcg(reinterpret_cast<uint4*>(b1 + 2 * K), Ve1);
+            __stcg(reinterpret_cast<uint4*>(b1 + 3 * K), Vo1);
+        }
+    }
+}
+
+static const void* reg_pick(int threads)
+{
+    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512>)
+                         : reinterpret_cast<const void*>(&regdom_kernel<256>);
+}
+
+size_t regdom_smem_bytes(int threads, int max_local_pairs)
+{
+    // FL0, FL1: 2 x 2 x threads uint4; RV: 2 x threads uint4; RH: threads
+    // uint2; HB: 2 x threads u32; offsets (pairs + 2) ints; hulls (pairs) int2
+    size_t b = (size_t)threads * (16 * 6 + 8 + 8);
+    b += (size_t)(max_local_pairs + 2) * 4;
+    b = (b + 7) & ~(size_t)7;
+    b += (size_t)max_local_pairs * 8;
+    return b;
+}
+
+int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm)
+{
+    *blocks_per_sm = 0;
+    const void* k = reg_pick(threads);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return (int)e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem_bytes);
+    if (e != cudaSuccess) cudaGetLastError();
+    return (int)e;
+}
+
+int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t sweep0, uint32_t nsweeps,
+                  const DevRng& rng, unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
+                  uint32_t stride, const uint8_t* colours, void* stream)
+{
+    RegParams P;
+    P.rows0 = rows + g.row_words;
+    P.g = g;
+    P.stripe_lo = plan.stripe_lo;
+    P.hull = plan.hull;
+    P.halo = plan.halo;
+    P.colours = colours;
+    P.sweep0 = sweep0;
+    P.nsweeps = nsweeps;
+    P.rng = rng;
+    P.xbuf = plan.xbuf;
+    P.status = plan.status;
+    P.ring = ring;
+    P.counts = counts;
+    P.burn = burn;
+    P.stride = stride;
+    P.epoch = epoch;
+    void* args[] = {&P};
+    return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads), dim3(plan.ctas), dim3(plan.threads), args,
+                                            plan.smem_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // namespace tl
