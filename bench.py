@@ -57,6 +57,9 @@ WORKLOADS = {
 }
 UNIFORM_T = 1 << 31
 KERNEL_SOURCES = ["paper_1804_07250_gb300/csrc/tl_resident.cu", "paper_1804_07250_gb300/csrc/tl_device.cuh"]
+REG_SOURCES = ["paper_1804_07250_gb300/csrc/tl_regdom.cu", "paper_1804_07250_gb300/csrc/tl_device.cuh"]
+# plan kernel -> (ncu kernel name, sources whose hash keys the recorded traffic)
+RESIDENT_KERNELS = {2: ("resident_kernel", KERNEL_SOURCES), 3: ("regdom_kernel", REG_SOURCES)}
 BATCH_SOURCES = ["paper_1804_07250_gb300/csrc/tl_batch.cu", "paper_1804_07250_gb300/csrc/tl_device.cuh"]
 
 
@@ -326,7 +329,7 @@ def run_ours(args):
     # dominant kernel: the sweep launches of each step, timed with CUDA
     # events on their stream
     plan = chain.plan()
-    if plan["kernel"] == 2:
+    if plan["kernel"] in RESIDENT_KERNELS:
         # the library splits a run into launches of at most spl sweeps and at
         # most 60000 * halo / passes sweeps (16-bit exchange tags)
         per = max(1, 60000 * plan["halo"] // info.passes)
@@ -340,7 +343,9 @@ def run_ours(args):
     alg_bytes_launch = bytes_per_sweep * SWEEPS / k_launches_per_run
     peak, peak_kind = peaks()
     achieved = alg_bytes_launch / (k_ms / 1e3) / 1e9
-    traffic = recorded_traffic(wl["name"]) if plan["kernel"] == 2 else None
+    kname, ksrc = RESIDENT_KERNELS.get(plan["kernel"], ("pass_global_kernel", KERNEL_SOURCES))
+    traffic = recorded_traffic(wl["name"], ksrc, {"kernel": plan["kernel"]}) if plan["kernel"] in RESIDENT_KERNELS \
+        else None
 
     # end to end through the C-ABI with host buffers
     init_host = dom.initial_state()
@@ -389,11 +394,10 @@ def run_ours(args):
                 "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": traffic, "kernel": "resident_kernel" if plan["kernel"] == 2
-                             else "pass_global_kernel", "kernel_ms": k_ms,
+                             "traffic": traffic, "kernel": kname, "kernel_ms": k_ms,
                              "alg_bytes_per_launch": alg_bytes_launch,
                              "us_per_sweep": 1e3 * run_ms / run_launches / SWEEPS,
-                             "kernel_hash": kernel_hash(), "plan": plan},
+                             "kernel_hash": kernel_hash(ksrc), "plan": plan},
                 "clocks": clocks,
                 "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "attempts/s",

@@ -1373,12 +1373,27 @@ static int plan_regdom(tl_chain* c)
         const int lo = a > 0 ? std::max(0, a - hp) : a, hi = b < npairs ? std::min(npairs, b + hp) : b;
         return pre[hi] - pre[lo];
     };
+    // Work of one exchange cycle, in warp-passes: threads take the held
+    // groups of the stripe's local pairs in order, 32 to a warp, and a warp
+    // runs in the passes where any of its pairs is still useful (owned pairs
+    // every pass; halo pair k below the stripe in the first h - (2k - 1)
+    // passes, above it in the first h - (2k - 2)).  The slowest stripe sets
+    // the pace of all, since neighbours wait for each other at every exchange.
     auto cost = [&](int a, int b) {
-        long v = (long)h * (pre[b] - pre[a]);
-        for (int k = 1; k <= hp; ++k) {
-            if (a > 0 && a - k >= 0) v += w[a - k] * (h - (2 * k - 1));
-            if (b < npairs && b + k - 1 < npairs) v += w[b + k - 1] * (h - (2 * k - 2));
+        const int plo = a > 0 ? std::max(0, a - hp) : a, phi = b < npairs ? std::min(npairs, b + hp) : b;
+        long v = 0, t = 0;
+        int warp_min = h;   // smallest halo distance in the current warp
+        for (int q = plo; q < phi; ++q) {
+            const int d = q < a ? 2 * (a - q) - 1 : (q >= b ? 2 * (q - b) : 0);
+            for (long i = 0; i < w[q]; ++i) {
+                warp_min = std::min(warp_min, d);
+                if (++t % 32 == 0) {
+                    v += std::max(0, h - warp_min);
+                    warp_min = h;
+                }
+            }
         }
+        if (t % 32) v += std::max(0, h - warp_min);
         return v;
     };
     // greedy stripes under a cost bound; bounds empty if infeasible

@@ -101,9 +101,9 @@ def test_default_plan_is_register_resident(T, ctx):
     ch = T.Chain(ctx, T.Domain.aztec(2048), seed=7, th=T.thresholds(scalar=T_HALF))
     plan = ch.plan()
     assert plan["kernel"] == 3, plan
-    # other thresholds keep the shared-memory resident kernel
+    # other thresholds take one of the general kernels
     ch2 = T.Chain(ctx, T.Domain.aztec(2048), seed=7, th=T.thresholds(scalar=0x7FFFFFFF))
-    assert ch2.plan()["kernel"] == 2
+    assert ch2.plan()["kernel"] in (1, 2)
 
 
 def test_density_and_nsew(T, ctx):
