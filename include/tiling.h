@@ -96,7 +96,10 @@ const char* tl_version(void);
 /* ------------------------------------------------------------------------
  * Context: one per GPU.  cuda_device is the CUDA ordinal.  The context
  * records the device's SM count and shared-memory limits used by the
- * launch planner.  Errors: TL_EINVAL (bad ordinal), TL_ECUDA.
+ * launch planner.  tl_ctx_destroy releases the caller's handle; chains and
+ * batches created on the context hold it too, and it is freed when the last
+ * of them is destroyed, in any order.  Errors: TL_EINVAL (bad ordinal),
+ * TL_ECUDA.
  * ---------------------------------------------------------------------- */
 int tl_ctx_create(int cuda_device, tl_ctx** out);
 void tl_ctx_destroy(tl_ctx* ctx);
@@ -452,6 +455,17 @@ uint64_t tl_chain_launches(const tl_chain* c);
  * between batch calls.
  * ---------------------------------------------------------------------- */
 typedef struct tl_batch tl_batch;
+
+/* Test hook for the failure path (no counterpart in the paper): raises the
+ * status word that the bounded waits of the resident kernels (chain `c`, if
+ * not NULL) and of the batched kernel (batch `b`, if not NULL) raise when they
+ * give up.  Their next launches stop at their first wait point (the next
+ * boundary exchange, the next tile) as if a wait had run out, so
+ * tl_chain_sync / tl_batch_hashes report TL_ETIMEOUT, clear the word, and
+ * leave the states undefined until tl_write_state or tl_chain_reset.
+ * Nothing waits longer and no fault is raised.  TL_EUNSUPPORTED if the chain
+ * runs on the per-pass kernel (it has no waits). */
+int tl_debug_raise_status(tl_chain* c, tl_batch* b);
 
 typedef struct {
     int tile_rows;          /* rows per tile (0 = keep) */

@@ -107,6 +107,7 @@ _SIG = {
     "tl_chain_set_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_sync": (_i, [_vp, _vp]),
+    "tl_debug_raise_status": (_i, [_vp, _vp]),
     "tl_run_sweeps": (_i, [_vp, _u64, _vp]),
     "tl_run_sweeps_hashed": (_i, [_vp, _u64, _vp, _vp]),
     "tl_read_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -382,6 +383,11 @@ class Chain:
     def sync(self, stream=None):
         _check(_lib.tl_chain_sync(self._h, _stream(stream)))
 
+    def debug_raise_status(self):
+        """Test hook: make the resident kernel's next launch stop at its first
+        boundary exchange as if a bounded wait had run out."""
+        _check(_lib.tl_debug_raise_status(self._h, None))
+
     def run(self, k: int, stream=None):
         _check(_lib.tl_run_sweeps(self._h, k, _stream(stream)))
 
@@ -485,6 +491,11 @@ class Batch:
 
     def run_per_chain(self, k: int, stream=None):
         _check(_lib.tl_batch_run_per_chain(self._h, k, _stream(stream)))
+
+    def debug_raise_status(self):
+        """Test hook: make the batched kernel's next launch stop before its
+        next tile as if a bounded wait had run out."""
+        _check(_lib.tl_debug_raise_status(None, self._h))
 
     def hashes(self, out=None, stream=None):
         if out is None:

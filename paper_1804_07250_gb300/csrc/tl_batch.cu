@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchChain* __restr
     __syncthreads();
     uint32_t parity = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(cursor, 1u);
+        // a raised status word (a wait that gave up elsewhere, or raised by
+        // the host) stops the block before it issues another copy
+        if (threadIdx.x == 0) s_tile = *(volatile int*)status ? ntiles : (int)atomicAdd(cursor, 1u);
         __syncthreads();
         const int t = s_tile;
         __syncthreads();
@@ -151,9 +153,15 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchChain* __restr
         const int arrived = __syncthreads_and(mbar_wait_bounded(&s_bar, parity) ? 1 : 0);
         parity ^= 1u;
         if (!arrived) {
-            // the copy did not complete in two seconds: report and stop (every
-            // thread of the block takes this branch together)
-            if (threadIdx.x == 0) atomicExch(status, 1);
+            // the copy did not complete in two seconds: report, give the copy
+            // one more bounded wait so that nothing is left writing this
+            // block's shared memory, and stop (every thread of the block
+            // takes this branch together)
+            if (threadIdx.x == 0) {
+                atomicExch(status, 1);
+                mbar_wait_bounded(&s_bar, parity ^ 1u);
+            }
+            __syncthreads();
             return;
         }
         const uint32_t sweep0 = *ch.sweep_base + sweep_off;

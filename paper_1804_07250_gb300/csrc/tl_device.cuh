@@ -568,4 +568,19 @@ TL_DEV void word_count_sliced(uint32_t w, int64_t i, int64_t plane_words, uint32
     }
 }
 
+// The same add for four consecutive words (index i a multiple of 4): one
+// 16-byte read and write per counter plane, the four carries rippling
+// together, so a thread's counter update is one chain of dependent accesses
+// per four words instead of per word.
+TL_DEV void word_count_sliced4(uint4 w, int64_t i, int64_t plane_words, uint32_t* cplanes)
+{
+    uint4 carry = w;
+    for (int b = 0; b < 32 && any4(carry); ++b) {
+        uint4* p = reinterpret_cast<uint4*>(cplanes + (int64_t)b * plane_words + i);
+        const uint4 c = *p;
+        *p = x4(c, carry);
+        carry = make_uint4(carry.x & c.x, carry.y & c.y, carry.z & c.z, carry.w & c.w);
+    }
+}
+
 }  // namespace tl

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,6 +75,9 @@ struct ShuffleCache {
 };
 
 struct tl_ctx {
+    // one reference for the caller's handle and one per chain or batch on
+    // the context: it is freed when the last of them goes, whatever the order
+    std::atomic<int> refs{1};
     int device;
     int sms;
     int smem_optin;
@@ -107,9 +111,9 @@ TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
     return TL_OK;
 }
 
-TL_API void tl_ctx_destroy(tl_ctx* c)
+static void ctx_release(tl_ctx* c)
 {
-    if (!c) return;
+    if (!c || c->refs.fetch_sub(1) != 1) return;
     if (c->shuffle.n) {
         cudaSetDevice(c->device);
         cudaDeviceSynchronize();
@@ -117,6 +121,8 @@ TL_API void tl_ctx_destroy(tl_ctx* c)
     }
     delete c;
 }
+
+TL_API void tl_ctx_destroy(tl_ctx* c) { ctx_release(c); }
 
 // ---------------------------------------------------------------------------
 // Domains
@@ -981,7 +987,9 @@ static void chain_free(tl_chain* c)
     cudaFree(c->xbuf_d);
     cudaFree(c->status_d);
     cudaFree(c->hull_d);
+    tl_ctx* ctx = c->ctx;
     delete c;
+    ctx_release(ctx);
 }
 
 static bool is_device_ptr(const void* p)
@@ -1051,6 +1059,7 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
     tl_chain* c = new (std::nothrow) tl_chain();
     if (!c) return fail(TL_ENOMEM, "tl_chain_create: host allocation");
     c->ctx = ctx;
+    ctx->refs.fetch_add(1);
     c->g = g;
     c->sites = d->sites;
     c->kappa = d->kappa;
@@ -1742,6 +1751,22 @@ TL_API int tl_chain_sync(tl_chain* c, void* stream)
     return TL_OK;
 }
 
+static int batch_raise_status(tl_batch* b);
+
+TL_API int tl_debug_raise_status(tl_chain* c, tl_batch* b)
+{
+    if (!c && !b) return fail(TL_EINVAL, "tl_debug_raise_status: NULL argument");
+    const int one = 1;
+    if (c) {
+        CUDA_TRY(cudaSetDevice(c->ctx->device));
+        if (!want_resident(c) || !c->status_d)
+            return fail(TL_EUNSUPPORTED, "tl_debug_raise_status: the chain has no resident kernel");
+        CUDA_TRY(cudaMemcpy(c->status_d, &one, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (b) TL_TRY(batch_raise_status(b));
+    return TL_OK;
+}
+
 TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream)
 {
     if (!c || (!ring && k)) return fail(TL_EINVAL, "tl_run_sweeps_hashed: NULL argument");
@@ -2132,6 +2157,15 @@ struct tl_batch {
     bool no_graph = false;
 };
 
+static int batch_raise_status(tl_batch* b)
+{
+    CUDA_TRY(cudaSetDevice(b->ctx->device));
+    const int one = 1;
+    CUDA_TRY(cudaMemcpy(b->d_status, &one, sizeof(int), cudaMemcpyHostToDevice));
+    return TL_OK;
+}
+
+
 static void batch_free_plan(tl_batch* b)
 {
     cudaFree(b->d_tiles_lpt);
@@ -2152,7 +2186,9 @@ static void batch_free(tl_batch* b)
     cudaFree(b->d_cursor);
     cudaFree(b->d_hash);
     cudaFree(b->d_status);
+    tl_ctx* ctx = b->ctx;
     delete b;
+    ctx_release(ctx);
 }
 
 // Tiles of height tile_rows for every chain; shared memory for tile + halo.
@@ -2275,6 +2311,7 @@ TL_API int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_ba
     tl_batch* b = new (std::nothrow) tl_batch();
     if (!b) return fail(TL_ENOMEM, "tl_batch_create: host allocation");
     b->ctx = ctx;
+    ctx->refs.fetch_add(1);
     b->ncursor = 1024;
     int rc = dev_alloc(&b->d_cursor, (size_t)b->ncursor, "cursors");
     if (rc == TL_OK) rc = dev_alloc(&b->d_status, 1, "status");
@@ -2492,7 +2529,10 @@ TL_API int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream)
         CUDA_TRY(cudaStreamSynchronize(SS(stream)));
         int st = 0;
         CUDA_TRY(cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (st) return fail(TL_ETIMEOUT, "batch: a tile's bulk copy did not complete; chain states are undefined");
+        if (st) {
+            CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+            return fail(TL_ETIMEOUT, "batch: a bounded wait gave up; chain states are undefined");
+        }
     }
     return TL_OK;
 }

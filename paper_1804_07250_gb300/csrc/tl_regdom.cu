@@ -297,16 +297,14 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 #pragma unroll
                             for (int pl = 0; pl < 4; ++pl) {
                                 const uint4 v4 = pw.v[4 * r + pl];
+                                if (sample && any4(v4))
+                                    word_count_sliced4(v4, (int64_t)y * RW + (int64_t)pl * K + k0,
+                                                       (int64_t)g.H * RW, P.counts);
+                                if (!P.ring) continue;
                                 const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                                for (int w = 0; w < 4; ++w) {
-                                    const uint32_t v = vv[w];
-                                    if (!v) continue;
-                                    if (P.ring) acc += word_hash(v, g, y, pl, k0 + w);
-                                    if (sample)
-                                        word_count_sliced(v, (int64_t)y * RW + (int64_t)pl * K + k0 + w,
-                                                          (int64_t)g.H * RW, P.counts);
-                                }
+                                for (int w = 0; w < 4; ++w)
+                                    if (vv[w]) acc += word_hash(vv[w], g, y, pl, k0 + w);
                             }
                         }
                     }
@@ -399,7 +397,9 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
             RV[2 * tid + 1] = Vo1;
             RH[tid] = make_uint2(Ho0.w, Ho1.w);
         }
-        if (tid == 0) s_ok = 1;
+        // a status word raised anywhere (a wait that gave up in another CTA,
+        // or raised by the host) ends every CTA at its next exchange
+        if (tid == 0) s_ok = *(volatile int*)P.status ? 0 : 1;
         __syncthreads();
         if (!ok) s_ok = 0;
         __syncthreads();

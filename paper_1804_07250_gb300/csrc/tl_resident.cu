@@ -431,7 +431,9 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 }
             }
         }
-        if (tid == 0) s_ok = 1;
+        // a status word raised anywhere (a wait that gave up in another CTA,
+        // or raised by the host) ends every CTA at its next exchange
+        if (tid == 0) s_ok = *(volatile int*)P.status ? 0 : 1;
         __syncthreads();
         if (!ok) s_ok = 0;
         __syncthreads();
