@@ -104,6 +104,15 @@ const char* tl_version(void);
 int tl_ctx_create(int cuda_device, tl_ctx** out);
 void tl_ctx_destroy(tl_ctx* ctx);
 
+/* Context options.  max_sms: use at most this many SMs for the resident
+ * kernels' stripes and the batched kernel's grid (0 = all), leaving the rest
+ * of the GPU to other work; results never depend on it.  Errors as
+ * tl_ctx_create, and TL_EINVAL for a negative field. */
+typedef struct {
+    int max_sms;
+} tl_ctx_opts;
+int tl_ctx_create_opts(int cuda_device, const tl_ctx_opts* opts, tl_ctx** out);
+
 /* ------------------------------------------------------------------------
  * Domains (Sec. 1.1: a simply-connected union of lattice faces; Sec. 1.2.1
  * lozenge hexagon; Sec. 1.2.4 six-vertex box with fixed boundary).
@@ -294,6 +303,26 @@ int tl_chain_set_order(tl_chain* c, int order);
  * from the past uses it to place runs at negative times.  Sweeps run after a
  * seek must stay below 2^32.  Errors: TL_EINVAL. */
 int tl_chain_seek(tl_chain* c, uint64_t sweep);
+
+/* Checkpoints (the position and inputs of RandomWalk, Sec. 2.2, carried
+ * across processes).  tl_checkpoint waits for the device, then writes into
+ * `out` a library-allocated byte string (free it with tl_blob_free) holding
+ * the lattice and box, seed, stream id, next sweep index, pass order,
+ * thresholds as given to tl_chain_create, the chain's starting tiling and
+ * its current tiling; layout: a fixed header, then the two canonical states,
+ * then the per-site thresholds (if any), in the host's byte order.  Density
+ * counters and the launch plan are not saved.  tl_restore builds on `ctx` a
+ * new chain with the same domain (the faces its starting tiling covers; the
+ * six-vertex square from its size), inputs, state and sweep index, so that
+ * running k sweeps on it gives exactly what the original would have.
+ * Errors: TL_EINVAL (NULL, not a checkpoint, corrupt), TL_ENOMEM, TL_ECUDA. */
+typedef struct {
+    void* data;
+    size_t size;
+} tl_blob;
+int tl_checkpoint(tl_chain* c, tl_blob* out);
+int tl_restore(tl_ctx* ctx, const tl_blob* blob, tl_chain** out);
+void tl_blob_free(tl_blob* b);
 
 /* Exact uniform random tiling of the Aztec diamond of order n (1 <= n <=
  * 32767) by domino shuffling (the shuffling algorithms of Sec. 3; Elkies,

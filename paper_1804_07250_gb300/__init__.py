@@ -68,6 +68,10 @@ class BatchPlan(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Blob(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("size", ctypes.c_size_t)]
+
+
 class Thresholds(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("scalar", ctypes.c_uint32),
                 ("site", ctypes.c_void_p), ("table16", ctypes.c_uint32 * 16)]
@@ -108,6 +112,10 @@ _SIG = {
     "tl_chain_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_sync": (_i, [_vp, _vp]),
     "tl_debug_raise_status": (_i, [_vp, _vp]),
+    "tl_checkpoint": (_i, [_vp, _vp]),
+    "tl_ctx_create_opts": (_i, [ctypes.c_int, _vp, _vp]),
+    "tl_restore": (_i, [_vp, _vp, _vp]),
+    "tl_blob_free": (None, [_vp]),
     "tl_run_sweeps": (_i, [_vp, _u64, _vp]),
     "tl_run_sweeps_hashed": (_i, [_vp, _u64, _vp, _vp]),
     "tl_read_state": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
@@ -171,10 +179,18 @@ def _ptr(buf):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+class CtxOpts(ctypes.Structure):
+    _fields_ = [("max_sms", ctypes.c_int)]
+
+
 class Context:
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, max_sms: int = 0):
         h = _vp()
-        _check(_lib.tl_ctx_create(device, ctypes.byref(h)))
+        if max_sms:
+            o = CtxOpts(max_sms)
+            _check(_lib.tl_ctx_create_opts(device, ctypes.byref(o), ctypes.byref(h)))
+        else:
+            _check(_lib.tl_ctx_create(device, ctypes.byref(h)))
         self._h = h
         self.device = device
 
@@ -382,6 +398,29 @@ class Chain:
 
     def sync(self, stream=None):
         _check(_lib.tl_chain_sync(self._h, _stream(stream)))
+
+    def checkpoint(self) -> bytes:
+        """The chain's inputs, start, state and sweep index as bytes
+        (tl_checkpoint); waits for the device."""
+        b = Blob()
+        _check(_lib.tl_checkpoint(self._h, ctypes.byref(b)))
+        try:
+            return ctypes.string_at(b.data, b.size)
+        finally:
+            _lib.tl_blob_free(ctypes.byref(b))
+
+    @classmethod
+    def restore(cls, ctx: "Context", blob: bytes, domain: "Domain | None" = None) -> "Chain":
+        """A new chain on `ctx` continuing exactly where the checkpointed one
+        stood (tl_restore).  `domain` (the same domain, optional) only gives
+        read_state and friends their default output shapes."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        b = Blob(ctypes.cast(buf, ctypes.c_void_p), len(blob))
+        h = _vp()
+        _check(_lib.tl_restore(ctx._h, ctypes.byref(b), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.ctx, self.domain, self._th, self._h = ctx, domain, None, h
+        return self
 
     def debug_raise_status(self):
         """Test hook: make the resident kernel's next launch stop at its first

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -85,6 +86,15 @@ struct tl_ctx {
     std::mutex shuffle_mu;   // one shuffling sample at a time per context
     ShuffleCache shuffle;
 };
+
+TL_API int tl_ctx_create_opts(int cuda_device, const tl_ctx_opts* opts, tl_ctx** out)
+{
+    if (opts && opts->max_sms < 0) return fail(TL_EINVAL, "tl_ctx_create_opts: max_sms < 0");
+    const int rc = tl_ctx_create(cuda_device, out);
+    if (rc != TL_OK || !opts) return rc;
+    if (opts->max_sms > 0) (*out)->sms = std::min((*out)->sms, opts->max_sms);
+    return TL_OK;
+}
 
 TL_API int tl_ctx_create(int cuda_device, tl_ctx** out)
 {
@@ -962,6 +972,10 @@ struct tl_chain {
     size_t colours_cap = 0;
     unsigned int epoch = 0;
     std::string res_why;
+    // thresholds as given, for checkpoints
+    int thr_api_kind = 0;
+    std::vector<uint32_t> thr_site;    // TL_T_SITE: [H][W]
+    uint32_t thr_table16[16] = {};
     // register-resident domino kernel (dominoes at t = 2^31)
     bool use_reg = false;
     RegPlan reg{};
@@ -1089,6 +1103,9 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
     }
     // thresholds
     c->th.kind = th->kind == TL_T_SITE ? THR_SITE : (th->kind == TL_T_TABLE16 ? THR_TABLE : THR_SCALAR);
+    c->thr_api_kind = th->kind;
+    if (th->kind == TL_T_TABLE16)
+        for (int i = 0; i < 16; ++i) c->thr_table16[i] = th->table16[i];
     c->th.scalar = th->scalar;
     c->th.kmax = th->scalar ? 31 - __builtin_ctz(th->scalar) : -1;
     c->th.planes = nullptr;
@@ -1134,6 +1151,9 @@ TL_API int tl_chain_create(tl_ctx* ctx, const tl_domain* d, const uint8_t* canon
         }
         e = cudaMemcpy(tdev, th->site, sizeof(uint32_t) * g.W * g.H,
                        is_device_ptr(th->site) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+        c->thr_site.resize((size_t)g.W * g.H);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->thr_site.data(), tdev, sizeof(uint32_t) * g.W * g.H, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = (cudaError_t)launch_threshold_planes(g, tdev, c->tplanes, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(tdev);
@@ -1386,23 +1406,34 @@ static int plan_regdom(tl_chain* c)
     // groups of the stripe's local pairs in order, 32 to a warp, and a warp
     // runs in the passes where any of its pairs is still useful (owned pairs
     // every pass; halo pair k below the stripe in the first h - (2k - 1)
-    // passes, above it in the first h - (2k - 2)).  The slowest stripe sets
-    // the pace of all, since neighbours wait for each other at every exchange.
+    // passes, above it in the first h - (2k - 2)).  A pass costs at least
+    // as much as four warps (one per scheduler: below that it is bound by
+    // the latency of one warp's chain, not by issue).  The slowest stripe
+    // sets the pace of all, since neighbours wait for each other at every
+    // exchange.
+    std::vector<int> live(h + 1);
     auto cost = [&](int a, int b) {
         const int plo = a > 0 ? std::max(0, a - hp) : a, phi = b < npairs ? std::min(npairs, b + hp) : b;
-        long v = 0, t = 0;
+        std::fill(live.begin(), live.end(), 0);   // live[p]: warps whose useful passes are the first p
+        long t = 0;
         int warp_min = h;   // smallest halo distance in the current warp
         for (int q = plo; q < phi; ++q) {
             const int d = q < a ? 2 * (a - q) - 1 : (q >= b ? 2 * (q - b) : 0);
             for (long i = 0; i < w[q]; ++i) {
                 warp_min = std::min(warp_min, d);
                 if (++t % 32 == 0) {
-                    v += std::max(0, h - warp_min);
+                    live[std::max(0, h - warp_min)] += 1;
                     warp_min = h;
                 }
             }
         }
-        if (t % 32) v += std::max(0, h - warp_min);
+        if (t % 32) live[std::max(0, h - warp_min)] += 1;
+        long v = 0;
+        int active = 0;   // warps running in pass ip, counted from the last pass down
+        for (int ip = h; ip >= 1; --ip) {
+            active += live[ip];
+            v += std::max(4, active);
+        }
         return v;
     };
     // greedy stripes under a cost bound; bounds empty if infeasible
@@ -1947,6 +1978,139 @@ TL_API int tl_chain_seek(tl_chain* c, uint64_t sweep)
 {
     if (!c || sweep > 0xFFFFFFFFull) return fail(TL_EINVAL, "tl_chain_seek: bad argument");
     c->sweep = sweep;
+    return TL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the chain's inputs and position (RandomWalk's state carried
+// between calls, Sec. 2.2) in one self-describing byte string.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint32_t kBlobMagic = 0x4B434C54u;   // "TLCK"
+constexpr uint32_t kBlobVersion = 1;
+struct BlobHead {
+    uint32_t magic, version;
+    int32_t lattice, W, H, N, kappa, random_order;
+    uint64_t seed, sweep;
+    uint32_t stream_id;
+    int32_t thr_kind;
+    uint32_t thr_scalar;
+    uint32_t table16[16];
+    uint64_t canon_bytes, site_words;
+};
+}  // namespace
+
+TL_API int tl_checkpoint(tl_chain* c, tl_blob* out)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_checkpoint: NULL argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    const Geom& g = c->g;
+    const size_t ncanon = (size_t)g.ntype * g.W * g.H;
+    BlobHead hd{};
+    hd.magic = kBlobMagic;
+    hd.version = kBlobVersion;
+    hd.lattice = g.lattice;
+    hd.W = g.W;
+    hd.H = g.H;
+    hd.N = g.N;
+    hd.kappa = c->kappa;
+    hd.random_order = c->random_order;
+    hd.seed = c->seed;
+    hd.sweep = c->sweep;
+    hd.stream_id = c->stream_id;
+    hd.thr_kind = c->thr_api_kind;
+    hd.thr_scalar = c->th.scalar;
+    for (int i = 0; i < 16; ++i) hd.table16[i] = c->thr_table16[i];
+    hd.canon_bytes = ncanon;
+    hd.site_words = c->thr_site.size();
+    const size_t size = sizeof(hd) + 2 * ncanon + 4 * hd.site_words;
+    uint8_t* buf = static_cast<uint8_t*>(std::malloc(size));
+    if (!buf) return fail(TL_ENOMEM, "tl_checkpoint: %zu bytes", size);
+    std::memcpy(buf, &hd, sizeof(hd));
+    uint8_t* start = buf + sizeof(hd);
+    uint8_t* cur = start + ncanon;
+    cudaError_t e = (cudaError_t)launch_unpack(g, c->rows0, c->canon, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(start, c->canon, ncanon, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = (cudaError_t)launch_unpack(g, c->rows, c->canon, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(cur, c->canon, ncanon, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        std::free(buf);
+        return fail(TL_ECUDA, "tl_checkpoint: %s", cudaGetErrorString(e));
+    }
+    c->launches += 2;
+    if (hd.site_words) std::memcpy(cur + ncanon, c->thr_site.data(), 4 * hd.site_words);
+    out->data = buf;
+    out->size = size;
+    return TL_OK;
+}
+
+TL_API void tl_blob_free(tl_blob* b)
+{
+    if (!b) return;
+    std::free(b->data);
+    b->data = nullptr;
+    b->size = 0;
+}
+
+TL_API int tl_restore(tl_ctx* ctx, const tl_blob* blob, tl_chain** out)
+{
+    if (!ctx || !blob || !blob->data || !out) return fail(TL_EINVAL, "tl_restore: NULL argument");
+    BlobHead hd;
+    if (blob->size < sizeof(hd)) return fail(TL_EINVAL, "tl_restore: blob too short");
+    std::memcpy(&hd, blob->data, sizeof(hd));
+    if (hd.magic != kBlobMagic || hd.version != kBlobVersion)
+        return fail(TL_EINVAL, "tl_restore: not a checkpoint of this library version");
+    if (hd.lattice < 0 || hd.lattice > 2 || !box_ok(hd.W, hd.H) || hd.thr_kind < 0 || hd.thr_kind > 2 ||
+        hd.sweep > 0xFFFFFFFFull || (hd.random_order != 0 && hd.random_order != 1))
+        return fail(TL_EINVAL, "tl_restore: corrupt header");
+    const int ntype = hd.lattice == LAT_LOZENGE ? 3 : 2;
+    const uint64_t ncanon = (uint64_t)ntype * hd.W * hd.H;
+    const uint64_t want_sites = hd.thr_kind == TL_T_SITE ? (uint64_t)hd.W * hd.H : 0;
+    if (hd.canon_bytes != ncanon || hd.site_words != want_sites ||
+        blob->size != sizeof(hd) + 2 * ncanon + 4 * want_sites)
+        return fail(TL_EINVAL, "tl_restore: sizes do not match the header");
+    const uint8_t* start = static_cast<const uint8_t*>(blob->data) + sizeof(hd);
+    const uint8_t* cur = start + ncanon;
+    // the domain: the six-vertex square from its size, a domino or lozenge
+    // domain from the faces its starting tiling covers
+    tl_domain* d = nullptr;
+    int rc;
+    if (hd.lattice == LAT_SIXV) {
+        if (hd.N < 1 || hd.W != hd.N + 2 || hd.H != hd.N + 2) return fail(TL_EINVAL, "tl_restore: corrupt header");
+        rc = tl_domain_dwbc(hd.N, &d);
+    } else {
+        d = new (std::nothrow) tl_domain();
+        if (!d) return fail(TL_ENOMEM, "tl_restore: host allocation");
+        d->g = make_geom(hd.lattice, hd.W, hd.H, 0);
+        d->init.assign(start, start + ncanon);
+        rc = finish_domain(d, 0, &d);
+        if (rc == TL_OK) d->kappa = hd.kappa;
+    }
+    if (rc != TL_OK) return rc;
+    tl_thresholds th{};
+    th.kind = hd.thr_kind;
+    th.scalar = hd.thr_scalar;
+    for (int i = 0; i < 16; ++i) th.table16[i] = hd.table16[i];
+    std::vector<uint32_t> site;
+    if (want_sites) {
+        site.resize(want_sites);
+        std::memcpy(site.data(), cur + ncanon, 4 * want_sites);
+        th.site = site.data();
+    }
+    tl_chain* c = nullptr;
+    rc = tl_chain_create(ctx, d, start, hd.seed, hd.stream_id, &th, &c);
+    tl_domain_destroy(d);
+    if (rc != TL_OK) return rc;
+    c->kappa = hd.kappa;
+    c->random_order = hd.random_order;
+    c->sweep = hd.sweep;
+    rc = tl_write_state(c, cur, ncanon, nullptr);
+    if (rc != TL_OK) {
+        tl_chain_destroy(c);
+        return rc;
+    }
+    *out = c;
     return TL_OK;
 }
 

@@ -121,3 +121,25 @@ def test_glauber_keeps_the_exact_law_and_reaches_it(T, ctx):
     ch2.run(6 * n * n)
     ff_burn, _ = frozen_fraction(ch2.read_state(), n)
     assert abs(ff_burn - ff_exact) < 0.03, (ff_burn, ff_exact)
+
+
+def test_chain_reaches_the_arctic_circle_at_order_1024(T, ctx):
+    # the heat-bath chain itself (t = 2^31), from the all-horizontal tiling,
+    # after 6 n^2 sweeps: frozen fraction within 0.02 of 1 - pi/4, north
+    # brickwork in the top cap, the frozen boundary crossing the vertical
+    # axis near n / sqrt 2
+    n = 1024
+    dom = T.Domain.aztec(n)
+    ch = T.Chain(ctx, dom, seed=2025, stream_id=1, th=T.thresholds(scalar=1 << 31))
+    ch.run(6 * n * n)
+    st = ch.read_state()
+    assert O.domino_check(st, _aztec_faces(n)) == 0
+    ff, t = frozen_fraction(st, n)
+    assert abs(ff - (1 - math.pi / 4)) < 0.02, ff
+    c = np.arange(2 * n) + 0.5 - n
+    X, Y = np.meshgrid(c, c)
+    cap = (t >= 0) & (np.hypot(X, Y) > 1.05 * n / math.sqrt(2)) & (Y > np.abs(X))
+    assert (t[cap] == 0).mean() >= 0.98
+    col = t[:, n]
+    ys = c[(col != 0) & (col >= 0)]
+    assert abs(ys.max() - n / math.sqrt(2)) < 0.02 * n + 16
