@@ -623,6 +623,50 @@ def run_exact(args):
         print(json.dumps(line), flush=True)
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(nprocs: int) -> int:
+    """Re-run this command as `nprocs` ranks (one process per GPU) under
+    torch.distributed.run on 127.0.0.1, when it was started as a single
+    process with --gpus N > 1; returns the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=%d" % nprocs,
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.abspath(__file__),
+           *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """Launcher check without GPUs: every rank times a small oracle replica
+    (its own stream id), the slowest rank's time is taken, and rank 0 prints
+    one line.  gloo on CPU, NCCL when every rank has a GPU."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    use_cuda = torch.cuda.is_available()
+    if world > 1:
+        if use_cuda:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    import oracle as O
+    from paper_1804_07250_gb300 import replicas
+    t0 = time.perf_counter()
+    st = O.aztec(16)
+    O.sweeps(O.DOMINO, st, seed=7, stream=replicas.replica_stream_id(0, rank, world), k=20, t_scalar=UNIFORM_T)
+    dt = replicas.max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None,
+                                 device="cuda" if use_cuda else "cpu")
+    hashes = replicas.gather_results(O.state_hash(st), dist if world > 1 else None)
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "ranks_seen": len(hashes),
+                          "distinct_streams": len(set(hashes)), "slowest_rank_s": dt}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -645,7 +689,16 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=BATCH_SWEEPS)
     ap.add_argument("--no-per-chain", action="store_true",
                     help="batch: skip the one-launch-per-chain comparison")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="check the rank launcher only (no GPU needed): a small oracle replica per rank")
     args = ap.parse_args()
+    # --gpus N started as one process: become N ranks (the driver may also
+    # start the ranks itself under torchrun, with WORLD_SIZE set)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus))
+    if args.dry_run:
+        run_dry(args)
+        return
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
         return

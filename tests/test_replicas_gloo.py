@@ -79,3 +79,22 @@ def test_single_process_fallbacks():
     assert R.replica_stream_id(5, 0, 1) == 5
     with pytest.raises(ValueError):
         R.shard([1], 2, 2)
+
+
+def test_bench_starts_its_own_ranks():
+    # `bench.py --gpus 2` started as one process re-runs itself as two ranks
+    # (torch.distributed.run on 127.0.0.1); the dry run needs no GPU: each
+    # rank samples its own replica and rank 0 reports both
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--dry-run"],
+                       capture_output=True, text=True, env=env, timeout=300, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    out = json.loads(lines[0])
+    assert out["n_gpus"] == 2 and out["ranks_seen"] == 2 and out["distinct_streams"] == 2
