@@ -475,6 +475,21 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
         per_chain = sites * kpc / (e0.elapsed_time(e1) / 1e3)
+    # 32 sampled chains (all of them if fewer) against the same chain run
+    # alone for the same number of sweeps: the batch must not change results
+    stream.synchronize()
+    hb = b.hashes()
+    pick = np.sort(np.random.default_rng(11).choice(len(chains), size=min(32, len(chains)), replace=False))
+    same = 0
+    for i in pick:
+        c = chains[int(i)]
+        alone = T.Chain(ctx, c.domain, seed=3, stream_id=int(i), th=T.thresholds(site=c.domain.domino_thresholds(
+            np.exp(0.5 * np.random.default_rng([3, int(i)]).standard_normal(
+                (2, 2 * int(orders[i]) + 1, 2 * int(orders[i]) + 1))))))
+        alone.run(c.sweep)
+        same += int(alone.state_hash() == int(hb[int(i)]))
+        alone.close()
+    assert same == len(pick), "batched chains differ from the same chains run alone"
     peak, peak_kind = peaks()
     us_sweep = 1e3 * total_ms / (args.steps * args.batch_sweeps)
     state_bytes = 2 * edges / 8
@@ -496,12 +511,13 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": state_bytes / (us_sweep * 1e-6) / 1e9, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": state_bytes / (us_sweep * 1e-6) / 1e9 / peak,
-                         "frac_state_plus_thresholds": (state_bytes + 4 * sites) / (us_sweep * 1e-6) / 1e9 / peak,
                          "us_per_sweep": us_sweep, "traffic": traffic, "kernel": "batch_kernel",
                          "sweeps_per_launch": bplan["sweeps_per_launch"],
                          "alg_bytes_per_launch": state_bytes * bplan["sweeps_per_launch"]},
             "batched_vs_per_chain": None if per_chain is None else
                 {"batched": value, "per_chain": per_chain, "speedup": value / per_chain, "per_chain_sweeps": kpc},
+            "sampled_check": {"chains": int(len(pick)), "equal_to_alone": same,
+                              "sweeps_each": int(chains[int(pick[0])].sweep)},
             "clocks": clocks, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
 
@@ -536,7 +552,8 @@ def run_serve(args):
         if label == "rate":
             rng = np.random.default_rng(11)
             pick = rng.choice(len(done), size=min(args.check, len(done)), replace=False)
-            same = sum(int(done[i].result_hash == serve.alone_hash(ctx, done[i].req)) for i in pick)
+            same = sum(int(done[i].status == "ok" and done[i].result_hash == serve.alone_hash(ctx, done[i].req))
+                       for i in pick)
             out["alone_vs_mixed"] = {"checked": int(len(pick)), "identical": int(same)}
     main_stats = out["rate"]
     line = {"metric": METRIC, "value": main_stats["attempts_per_s"], "unit": "attempts/s", "n_gpus": 1,
@@ -544,6 +561,7 @@ def run_serve(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "served_poisson_%g_per_s_%d_requests" % (args.rate, args.requests),
                        "budget_gb": args.budget_gb, "block": 100},
+            "clocks": main_stats.get("clocks"),
             "serve": out}
     print(json.dumps(line), flush=True)
 
