@@ -225,6 +225,13 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     const size_t side_words = (size_t)(h >> 1) * 32 * Kg;   // u64 per side
     uint64_t done = 0;
     int cyc = 0, buf = 0;
+    // the next density sample: sweeps s (counted after the sweep, 1-based)
+    // with s >= burn and (s - burn) % stride == 0, tracked incrementally
+    uint64_t next_sample = ~0ull;
+    if (P.counts && P.stride) {
+        const uint64_t first = (uint64_t)P.sweep0 + 1;
+        next_sample = first <= P.burn ? P.burn : P.burn + ((first - P.burn + P.stride - 1) / P.stride) * P.stride;
+    }
     uint32_t sweep = P.sweep0, slot = 0;
     // random words of the next pass, computed before the barrier of the
     // current one (they depend on no state)
@@ -284,8 +291,8 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
             buf ^= 1;
             if (slot == 1u) {
                 // end of a sweep: owned rows are exact
-                const uint64_t ndone = (uint64_t)sweep + 1;
-                const bool sample = P.counts && P.stride && ndone >= P.burn && (ndone - P.burn) % P.stride == 0;
+                const bool sample = (uint64_t)sweep + 1 == next_sample;
+                if (sample) next_sample += P.stride;
                 if (P.ring || sample) {
                     uint64_t acc = 0;
                     if (owned) {

@@ -227,6 +227,13 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
     const int rtid = upd_role ? tid : tid - HALF;
     uint64_t done = 0;
     int cyc = 0;
+    // the next density sample: sweeps s (counted after the sweep, 1-based)
+    // with s >= burn and (s - burn) % stride == 0, tracked incrementally
+    uint64_t next_sample = ~0ull;
+    if (P.counts && P.stride) {
+        const uint64_t first = (uint64_t)P.sweep0 + 1;
+        next_sample = first <= P.burn ? P.burn : P.burn + ((first - P.burn + P.stride - 1) / P.stride) * P.stride;
+    }
     uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
     // pass table of a cycle: item range, random-plane offset, pass slot |
     // colour << 8, sweep.  The slot keys the random numbers, the colour (the
@@ -320,9 +327,8 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             __syncthreads();
             if (slot == (uint32_t)(passes - 1)) {
                 // end of a sweep: the owned rows are exact (i < halo)
-                const uint64_t ndone = (uint64_t)sweep + 1;
-                const bool sample = P.counts && P.stride && ndone >= P.burn &&
-                                    (ndone - P.burn) % P.stride == 0;
+                const bool sample = (uint64_t)sweep + 1 == next_sample;
+                if (sample) next_sample += P.stride;
                 if (P.ring || sample) {
                     const int rw = (int)RW;
                     const int nw = (hi - lo) * rw;
