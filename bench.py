@@ -269,8 +269,8 @@ def run_ours(args):
     from paper_1804_07250_gb300 import replicas
     # every rank samples its own replica: same workload, its own stream id
     chain = T.Chain(ctx, dom, seed=wl["seed"], stream_id=replicas.replica_stream_id(0, rank, world), th=th)
-    if args.kernel or args.spl or args.halo or args.threads:
-        chain.set_plan(args.kernel, args.spl, args.halo, args.threads)
+    if args.kernel or args.spl or args.halo or args.threads or args.npre:
+        chain.set_plan(args.kernel, args.spl, args.halo, args.threads, args.npre)
     hshape = dom.height_shape
     density = wl["density"]
     height_dev = torch.empty(hshape, dtype=torch.int32, device="cuda")
@@ -695,6 +695,7 @@ def main():
     ap.add_argument("--spl", type=int, default=0, help="sweeps per launch (0 auto)")
     ap.add_argument("--halo", type=int, default=0, help="resident kernel halo (0 auto)")
     ap.add_argument("--threads", type=int, default=0, help="resident kernel threads (0 auto)")
+    ap.add_argument("--npre", type=int, default=0, help="random planes generated ahead (0 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="sweeps per step instead of the workload's (short runs for profiling only)")
