@@ -298,6 +298,17 @@ uint64_t tl_chain_sweep(const tl_chain* c);
 #define TL_ORDER_RANDOM 1
 int tl_chain_set_order(tl_chain* c, int order);
 
+/* Accepted-flip counter (a chain metric): after tl_chain_count_flips(c, 1)
+ * every site rotation that the chain's own sweeps perform (tl_run_sweeps,
+ * tl_run_sweeps_hashed; a site that changes orientation in a pass counts
+ * once) is added to a 64-bit device counter, which the call resets;
+ * tl_chain_count_flips(c, 0) stops counting.  tl_chain_flips waits for the
+ * device and reads the count.  Sweeps run inside a batch are not counted.
+ * The ratio flips / (sites x sweeps) is the chain's acceptance rate.
+ * Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_chain_count_flips(tl_chain* c, int on);
+int tl_chain_flips(tl_chain* c, uint64_t* out);
+
 /* Set the absolute index of the next sweep (0 .. 2^32 - 1).  Random numbers
  * are keyed by this index, so seeking replays or skips randomness; coupling
  * from the past uses it to place runs at negative times.  Sweeps run after a
@@ -528,8 +539,12 @@ int tl_batch_get_plan(tl_batch* b, tl_batch_plan* plan);
 /* Time every tile height in {32, 64, 128} x R in {1, 2, 4, 8} on the batch
  * itself for `trial_sweeps` sweeps (rounded up to a multiple of R), twice
  * each from the same states, and keep the plan with the fastest run; states
- * and sweep counters are restored afterwards. */
+ * and sweep counters are restored afterwards.  The result is cached per
+ * (lattices present, threshold kinds present, total rows rounded down to a
+ * power of two, SM count): a later batch with the same key takes the cached
+ * plan at once, without trials.  tl_autotune_cache_clear empties the cache. */
 int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, tl_batch_plan* out);
+void tl_autotune_cache_clear(void);
 uint64_t tl_batch_launches(const tl_batch* b);
 
 #ifdef __cplusplus

@@ -113,6 +113,9 @@ _SIG = {
     "tl_chain_sync": (_i, [_vp, _vp]),
     "tl_debug_raise_status": (_i, [_vp, _vp]),
     "tl_checkpoint": (_i, [_vp, _vp]),
+    "tl_autotune_cache_clear": (None, []),
+    "tl_chain_count_flips": (_i, [_vp, ctypes.c_int]),
+    "tl_chain_flips": (_i, [_vp, _vp]),
     "tl_ctx_create_opts": (_i, [ctypes.c_int, _vp, _vp]),
     "tl_restore": (_i, [_vp, _vp, _vp]),
     "tl_blob_free": (None, [_vp]),
@@ -380,6 +383,16 @@ class Chain:
     def seek(self, sweep: int):
         _check(_lib.tl_chain_seek(self._h, sweep))
 
+    def count_flips(self, on: bool = True):
+        """Start (and reset) or stop the accepted-flip counter."""
+        _check(_lib.tl_chain_count_flips(self._h, 1 if on else 0))
+
+    @property
+    def flips(self) -> int:
+        v = ctypes.c_uint64()
+        _check(_lib.tl_chain_flips(self._h, ctypes.byref(v)))
+        return int(v.value)
+
     def set_order(self, random: bool):
         """Fixed colour order per sweep, or a random colour for every pass slot."""
         _check(_lib.tl_chain_set_order(self._h, 1 if random else 0))
@@ -556,6 +569,10 @@ class Batch:
         p = BatchPlan()
         _check(_lib.tl_batch_autotune(self._h, trial_sweeps, _stream(stream), ctypes.byref(p)))
         return p.as_dict()
+
+    @staticmethod
+    def autotune_cache_clear():
+        _lib.tl_autotune_cache_clear()
 
     @property
     def launches(self) -> int:

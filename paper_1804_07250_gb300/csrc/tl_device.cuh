@@ -34,6 +34,7 @@ TL_DEV uint4 ld4(const uint32_t* p) { return *reinterpret_cast<const uint4*>(p);
 TL_DEV void st4(uint32_t* p, uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
 TL_DEV uint4 x4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
 TL_DEV bool any4(uint4 a) { return (a.x | a.y | a.z | a.w) != 0u; }
+TL_DEV uint32_t popc4(uint4 a) { return __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w); }
 
 // Site j of a plane shifted by one: bit j of the result is bit j-1 (shl) or
 // bit j+1 (shr) of the plane row, using the neighbouring words.
@@ -266,7 +267,7 @@ TL_DEV uint32_t range_mask(int k, int jlo, int jhi)
 // ---------------------------------------------------------------------------
 template <int TK, class RND>
 TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                          const RND& rnd, const ThrView& th)
+                          const RND& rnd, const ThrView& th, uint32_t* nflip = nullptr)
 {
     const int p = (int)((pass + (uint32_t)y) & 1u);
     const int k0 = m << 2;
@@ -302,6 +303,7 @@ TL_DEV void domino_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32
     const uint4 fl = make_uint4(f.x & (lt.x ^ E.x), f.y & (lt.y ^ E.y), f.z & (lt.z ^ E.z),
                                 f.w & (lt.w ^ E.w));
     if (!any4(fl)) return;
+    if (nflip) *nflip += popc4(fl);
     st4(pE, x4(E, fl));
     st4(pN, x4(N, fl));
     st4(pS, x4(S, fl));
@@ -325,6 +327,7 @@ struct DominoFast {
     int64_t soff;        // offset of the S plane row relative to base
     int K, p;
     uint4 He, Ho, N, S;  // new values
+    uint32_t nfl;        // sites of the group that flip
 };
 
 // `gp` points at plane 0, word k0 of the group's row.
@@ -357,6 +360,7 @@ TL_DEV DominoFast domino_fast_compute(uint32_t* gp, int64_t RW, int K, int p, in
     const uint32_t fln = fn & (~onext ^ En) & 1u;
     const uint4 sh = make_uint4((fl.x >> 1) | (fl.y << 31), (fl.y >> 1) | (fl.z << 31),
                                 (fl.z >> 1) | (fl.w << 31), (fl.w >> 1) | (fln << 31));
+    r.nfl = popc4(fl);
     r.base = pHe;
     r.soff = -RW + (int64_t)(2 + p) * K;
     r.K = K;
@@ -385,7 +389,7 @@ TL_DEV void domino_fast_store(const DominoFast& r)
 // ---------------------------------------------------------------------------
 template <int TK, class RND>
 TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint32_t pass,
-                           const RND& rnd, const ThrView& th)
+                           const RND& rnd, const ThrView& th, uint32_t* nflip = nullptr)
 {
     const int r = (int)((pass + 3u - (uint32_t)(y % 3)) % 3u);
     const int k0 = m << 2;
@@ -426,6 +430,7 @@ TL_DEV void lozenge_update(uint32_t* row, int64_t RW, int K, int y, int m, uint3
     const uint4 fl = make_uint4(f.x & (lt.x ^ e0.x), f.y & (lt.y ^ e0.y), f.z & (lt.z ^ e0.z),
                                 f.w & (lt.w ^ e0.w));
     if (!any4(fl)) return;
+    if (nflip) *nflip += popc4(fl);
     st4(p0, x4(e0, fl));
     st4(p1, x4(e1, fl));
     st4(p2, x4(e2, fl));
@@ -451,7 +456,8 @@ TL_DEV int sixv_py(uint32_t pass) { return (pass == 1u || pass == 3u) ? 1 : 0; }
 
 template <class RND>
 TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, uint32_t pass,
-                        const RND& rnd, const ThrView& th, const uint32_t* ttab, const uint32_t* ctab)
+                        const RND& rnd, const ThrView& th, const uint32_t* ttab, const uint32_t* ctab,
+                        uint32_t* nflip = nullptr)
 {
     const int px = sixv_px(pass);
     const int k0 = m << 2;
@@ -507,6 +513,7 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
     const uint4 fl = make_uint4(f.x & (lt.x ^ B.x), f.y & (lt.y ^ B.y), f.z & (lt.z ^ B.z),
                                 f.w & (lt.w ^ B.w));
     if (!any4(fl)) return;
+    if (nflip) *nflip += popc4(fl);
     st4(pB, x4(B, fl));
     st4(pT, x4(T, fl));
     st4(pL, x4(L, fl));
@@ -517,15 +524,16 @@ TL_DEV void sixv_update(uint32_t* row, int64_t RW, int K, int N, int Y, int m, u
 
 // Dispatch one group update for lattice LAT.
 // `ttab`: expanded six-vertex table in shared memory, or nullptr; `ctab`:
-// expanded count table (used instead when not nullptr).
+// expanded count table (used instead when not nullptr).  `nflip`, if not
+// nullptr, is increased by the number of sites that flipped.
 template <int LAT, int TK, class RND>
 TL_DEV void group_update(uint32_t* row, int64_t RW, const Geom& g, int y, int m, uint32_t pass,
                          const RND& rnd, const ThrView& th, const uint32_t* ttab = nullptr,
-                         const uint32_t* ctab = nullptr)
+                         const uint32_t* ctab = nullptr, uint32_t* nflip = nullptr)
 {
-    if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
-    else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, rnd, th);
-    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th, ttab, ctab);
+    if (LAT == LAT_DOMINO) domino_update<TK>(row, RW, g.K, y, m, pass, rnd, th, nflip);
+    else if (LAT == LAT_LOZENGE) lozenge_update<TK>(row, RW, g.K, y, m, pass, rnd, th, nflip);
+    else sixv_update(row, RW, g.K, g.N, y, m, pass, rnd, th, ttab, ctab, nflip);
 }
 
 // splitmix64 output for state x (Steele, Lea & Flood 2014).

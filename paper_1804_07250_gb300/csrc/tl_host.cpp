@@ -5,6 +5,7 @@
 #include "tl_thurston.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -13,10 +14,24 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
+
+// NVTX ranges around the library's launches, graph blocks and exact
+// samplers, named after the C-ABI call (visible in Nsight Systems / ncu
+// with NVTX enabled; without a tool attached each costs a pointer check).
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace tl;
 
@@ -972,6 +987,9 @@ struct tl_chain {
     size_t colours_cap = 0;
     unsigned int epoch = 0;
     std::string res_why;
+    // accepted-flip counter (tl_chain_count_flips)
+    unsigned long long* flips_d = nullptr;
+    bool count_flips = false;
     // thresholds as given, for checkpoints
     int thr_api_kind = 0;
     std::vector<uint32_t> thr_site;    // TL_T_SITE: [H][W]
@@ -1001,6 +1019,7 @@ static void chain_free(tl_chain* c)
     cudaFree(c->xbuf_d);
     cudaFree(c->status_d);
     cudaFree(c->hull_d);
+    cudaFree(c->flips_d);
     tl_ctx* ctx = c->ctx;
     delete c;
     ctx_release(ctx);
@@ -1281,7 +1300,8 @@ static int run_segment(tl_chain* c, uint64_t n, void* stream)
         const uint32_t sw = (uint32_t)(c->sweep + s);
         for (int p = 0; p < g.passes; ++p) {
             const uint32_t colour = c->random_order ? slot_colour_host(c->rng, sw, (uint32_t)p, g.passes) : (uint32_t)p;
-            const int e = launch_pass_global(g, c->rows, colour, (uint32_t)p, sw, c->rng, c->th, c->grange, stream);
+            const int e = launch_pass_global(g, c->rows, colour, (uint32_t)p, sw, c->rng, c->th, c->grange,
+                                             c->count_flips ? c->flips_d : nullptr, stream);
             if (e) return fail(TL_ECUDA, "pass kernel: %s", cudaGetErrorString((cudaError_t)e));
         }
         c->launches += (uint64_t)g.passes;
@@ -1717,10 +1737,12 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
             c->use_reg
                 ? launch_regdom(c->g, c->rows, c->reg, (uint32_t)c->sweep, (uint32_t)n, c->rng, ++c->epoch,
                                 ring ? ring + done : nullptr, dens ? c->cplanes : nullptr, c->burn,
-                                dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream)
+                                dens ? c->stride : 0, c->random_order ? c->colours : nullptr,
+                                c->count_flips ? c->flips_d : nullptr, stream)
                 : launch_resident(c->g, c->rows, c->res, (uint32_t)c->sweep, (uint32_t)n, c->rng, c->th, c->grange,
                                   ++c->epoch, ring ? ring + done : nullptr, dens ? c->cplanes : nullptr, c->burn,
-                                  dens ? c->stride : 0, c->random_order ? c->colours : nullptr, stream);
+                                  dens ? c->stride : 0, c->random_order ? c->colours : nullptr,
+                                  c->count_flips ? c->flips_d : nullptr, stream);
         if (e) return fail(TL_ECUDA, "resident kernel: %s", cudaGetErrorString((cudaError_t)e));
         if (dens) c->samples += samples_upto(c, c->sweep + n) - samples_upto(c, c->sweep);
         c->sweep += n;
@@ -1742,6 +1764,7 @@ static int zero_counts_if_needed(tl_chain* c, void* stream)
 
 TL_API int tl_run_sweeps(tl_chain* c, uint64_t k, void* stream)
 {
+    NvtxRange nvtx_("tl_run_sweeps");
     if (!c) return fail(TL_EINVAL, "tl_run_sweeps: NULL chain");
     if (c->sweep + k > 0x100000000ull) return fail(TL_EINVAL, "tl_run_sweeps: sweep index beyond 2^32 - 1");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
@@ -1800,6 +1823,7 @@ TL_API int tl_debug_raise_status(tl_chain* c, tl_batch* b)
 
 TL_API int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream)
 {
+    NvtxRange nvtx_("tl_run_sweeps_hashed");
     if (!c || (!ring && k)) return fail(TL_EINVAL, "tl_run_sweeps_hashed: NULL argument");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     if (k) TL_TRY(require_local(ring, c->ctx->device, "tl_run_sweeps_hashed"));
@@ -1945,6 +1969,7 @@ static int shuffle_prepare(tl_ctx* ctx, int n)
 TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_id, uint8_t* canon, size_t cap,
                             void* stream)
 {
+    NvtxRange nvtx_("tl_aztec_shuffle");
     if (!ctx || !canon || n < 1 || n > 32767) return fail(TL_EINVAL, "tl_aztec_shuffle: bad argument");
     const size_t W = 2 * (size_t)n + 1, ncanon = 2 * W * W;
     if (cap < ncanon) return fail(TL_EINVAL, "tl_aztec_shuffle: cap %zu < %zu", cap, ncanon);
@@ -1971,6 +1996,34 @@ TL_API int tl_chain_set_order(tl_chain* c, int order)
 {
     if (!c || (order != TL_ORDER_FIXED && order != TL_ORDER_RANDOM)) return fail(TL_EINVAL, "tl_chain_set_order: bad argument");
     c->random_order = order == TL_ORDER_RANDOM;
+    return TL_OK;
+}
+
+TL_API int tl_chain_count_flips(tl_chain* c, int on)
+{
+    if (!c) return fail(TL_EINVAL, "tl_chain_count_flips: NULL chain");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (on && !c->flips_d) TL_TRY(dev_alloc(&c->flips_d, 1, "flip counter"));
+    if (on) {   // starting resets the count; stopping keeps it readable
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaMemset(c->flips_d, 0, sizeof(unsigned long long)));
+    }
+    c->count_flips = on != 0;
+    return TL_OK;
+}
+
+TL_API int tl_chain_flips(tl_chain* c, uint64_t* out)
+{
+    if (!c || !out) return fail(TL_EINVAL, "tl_chain_flips: NULL argument");
+    CUDA_TRY(cudaSetDevice(c->ctx->device));
+    if (!c->flips_d) {
+        *out = 0;
+        return TL_OK;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long v = 0;
+    CUDA_TRY(cudaMemcpy(&v, c->flips_d, sizeof(v), cudaMemcpyDeviceToHost));
+    *out = v;
     return TL_OK;
 }
 
@@ -2002,6 +2055,7 @@ struct BlobHead {
 
 TL_API int tl_checkpoint(tl_chain* c, tl_blob* out)
 {
+    NvtxRange nvtx_("tl_checkpoint");
     if (!c || !out) return fail(TL_EINVAL, "tl_checkpoint: NULL argument");
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     CUDA_TRY(cudaDeviceSynchronize());
@@ -2055,6 +2109,7 @@ TL_API void tl_blob_free(tl_blob* b)
 
 TL_API int tl_restore(tl_ctx* ctx, const tl_blob* blob, tl_chain** out)
 {
+    NvtxRange nvtx_("tl_restore");
     if (!ctx || !blob || !blob->data || !out) return fail(TL_EINVAL, "tl_restore: NULL argument");
     BlobHead hd;
     if (blob->size < sizeof(hd)) return fail(TL_EINVAL, "tl_restore: blob too short");
@@ -2121,6 +2176,7 @@ TL_API int tl_restore(tl_ctx* ctx, const tl_blob* blob, tl_chain** out)
 TL_API int tl_cftp(tl_ctx* ctx, const tl_domain* d, uint64_t seed, uint32_t stream_id, const tl_thresholds* th,
                    uint64_t t0, uint64_t tmax, uint8_t* canon_out, size_t cap, uint64_t* t_used, void* stream)
 {
+    NvtxRange nvtx_("tl_cftp");
     if (!ctx || !d || !th || !canon_out || t0 < 1 || tmax < t0 || tmax > 0x80000000ull)
         return fail(TL_EINVAL, "tl_cftp: bad argument");
     const size_t n = d->init.size();
@@ -2667,6 +2723,7 @@ static int batch_run(tl_batch* b, uint64_t k, void* stream, bool per_chain)
 
 TL_API int tl_batch_run(tl_batch* b, uint64_t k, void* stream)
 {
+    NvtxRange nvtx_("tl_batch_run");
     if (!b) return fail(TL_EINVAL, "tl_batch_run: NULL batch");
     return batch_run(b, k, stream, false);
 }
@@ -2732,10 +2789,51 @@ TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
 // Try tile heights x sweeps per launch on the batch itself, keep the fastest.
 // The chains' states and sweep counters are restored afterwards, so tuning
 // does not change any result.
+// Autotune results per (lattices present, threshold kinds present, rows of
+// the batch rounded down to a power of two, SMs): a batch like one already
+// tuned takes that plan without trials.
+namespace {
+using TuneKey = std::tuple<int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // -> (tile rows, sweeps per launch)
+TuneKey tune_key(const tl_batch* b)
+{
+    int lat = 0, thr = 0;
+    uint64_t rows = 0;
+    for (const tl_chain* c : b->chains) {
+        lat |= 1 << c->g.lattice;
+        thr |= 1 << c->th.kind;
+        rows += (uint64_t)c->g.H;
+    }
+    int bucket = 0;
+    while (rows > 1) {
+        rows >>= 1;
+        ++bucket;
+    }
+    return TuneKey(lat, thr, bucket, b->ctx->sms);
+}
+}  // namespace
+
+TL_API void tl_autotune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+}
+
 TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, tl_batch_plan* out)
 {
+    NvtxRange nvtx_("tl_batch_autotune");
     if (!b || trial_sweeps == 0) return fail(TL_EINVAL, "tl_batch_autotune: bad argument");
     CUDA_TRY(cudaSetDevice(b->ctx->device));
+    const TuneKey key = tune_key(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && batch_plan(b, it->second.first, it->second.second) == TL_OK) {
+            if (out) TL_TRY(tl_batch_get_plan(b, out));
+            return TL_OK;
+        }
+    }
     // snapshot every chain's state
     size_t total = 0;
     for (auto* c : b->chains) total += (size_t)c->g.total_words;
@@ -2808,6 +2906,10 @@ TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, t
     cudaFree(snap);
     if (rc != TL_OK) return rc;
     TL_TRY(batch_plan(b, best_t, best_r));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(best_t, best_r);
+    }
     if (out) TL_TRY(tl_batch_get_plan(b, out));
     return TL_OK;
 }

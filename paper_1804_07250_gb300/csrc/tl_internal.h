@@ -65,8 +65,10 @@ int launch_pack(const Geom& g, const uint8_t* canon_dev, uint32_t* rows, void* s
 int launch_unpack(const Geom& g, const uint32_t* rows, uint8_t* canon_dev, void* stream);
 // `pass`: the colour class updated; `slot`: the pass slot that keys the
 // random numbers (equal unless the pass order is random).
+// flips: accepted-flip counter (nullptr = not counted).
 int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t slot, uint32_t sweep,
-                       const DevRng& rng, const ThrView& th, const int2* grange, void* stream);
+                       const DevRng& rng, const ThrView& th, const int2* grange, unsigned long long* flips,
+                       void* stream);
 int launch_hash(const Geom& g, const uint32_t* rows, unsigned long long* out, void* stream);
 // Density counters are bit-sliced planes [32][H][row_words] (cplanes);
 // launch_density_decode writes the canonical counts [ntype][H][W] from them.
@@ -128,7 +130,7 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, const uint8_t* colours, void* stream);
+                    uint32_t stride, const uint8_t* colours, unsigned long long* flips, void* stream);
 // Colours of the pass slots of nsweeps sweeps under the random pass order.
 int launch_slot_colours(uint8_t* out, uint32_t sweep0, uint32_t nsweeps, int passes, const DevRng& rng, void* stream);
 
@@ -151,7 +153,7 @@ size_t regdom_smem_bytes(int threads, int max_local_pairs);
 int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm);
 int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t sweep0, uint32_t nsweeps,
                   const DevRng& rng, unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                  uint32_t stride, const uint8_t* colours, void* stream);
+                  uint32_t stride, const uint8_t* colours, unsigned long long* flips, void* stream);
 
 // ---- batched chains (tl_batch.cu) ----
 struct BatchChain {

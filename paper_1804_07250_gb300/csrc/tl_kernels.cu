@@ -30,7 +30,8 @@ template <int LAT, int TK>
 __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__ rows0, Geom g,
                                                           uint32_t pass, uint32_t slot, uint32_t sweep,
                                                           DevRng rng, ThrView th,
-                                                          const int2* __restrict__ grange)
+                                                          const int2* __restrict__ grange,
+                                                          unsigned long long* __restrict__ flips)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nrow = (LAT == LAT_SIXV) ? ((g.H + 1) >> 1) : g.H;
@@ -51,13 +52,16 @@ __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__
     const uint32_t grp = (uint32_t)(rr * g.Kg + m);
     uint32_t* row = rows0 + (int64_t)y * g.row_words;
     const RndPhilox rnd{grp, sweep, slot, rng};
-    group_update<LAT, TK>(row, g.row_words, g, y, m, pass, rnd, th);
+    uint32_t nfl = 0;
+    group_update<LAT, TK>(row, g.row_words, g, y, m, pass, rnd, th, nullptr, nullptr, flips ? &nfl : nullptr);
+    if (nfl) atomicAdd(flips, (unsigned long long)nfl);
 }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t slot, uint32_t sweep,
-                       const DevRng& rng, const ThrView& th, const int2* grange, void* stream)
+                       const DevRng& rng, const ThrView& th, const int2* grange, unsigned long long* flips,
+                       void* stream)
 {
     const int nrow = (g.lattice == LAT_SIXV) ? ((g.H + 1) >> 1) : g.H;
     const int64_t threads = (int64_t)nrow * g.Kg;
@@ -65,16 +69,16 @@ int launch_pass_global(const Geom& g, uint32_t* rows, uint32_t pass, uint32_t sl
     uint32_t* rows0 = rows + g.row_words;
     if (g.lattice == LAT_DOMINO) {
         if (th.kind == THR_SITE)
-            pass_global_kernel<LAT_DOMINO, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
+            pass_global_kernel<LAT_DOMINO, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange, flips);
         else
-            pass_global_kernel<LAT_DOMINO, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
+            pass_global_kernel<LAT_DOMINO, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange, flips);
     } else if (g.lattice == LAT_LOZENGE) {
         if (th.kind == THR_SITE)
-            pass_global_kernel<LAT_LOZENGE, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
+            pass_global_kernel<LAT_LOZENGE, THR_SITE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange, flips);
         else
-            pass_global_kernel<LAT_LOZENGE, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
+            pass_global_kernel<LAT_LOZENGE, THR_SCALAR><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange, flips);
     } else {
-        pass_global_kernel<LAT_SIXV, THR_TABLE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange);
+        pass_global_kernel<LAT_SIXV, THR_TABLE><<<blocks, 256, 0, S(stream)>>>(rows0, g, pass, slot, sweep, rng, th, grange, flips);
     }
     return (int)cudaGetLastError();
 }

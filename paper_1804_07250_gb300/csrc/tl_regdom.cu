@@ -48,6 +48,7 @@ struct RegParams {
     uint64_t burn;
     uint32_t stride;
     unsigned int epoch;
+    unsigned long long* flips;  // accepted-flip counter, or nullptr
 };
 
 TL_DEV uint64_t rd_globaltimer()
@@ -122,7 +123,9 @@ struct PairWords {
     uint4 v[8];
 };
 
-template <int NT>
+// COUNT: the chain counts its accepted flips (a separate instantiation, so
+// the default path carries no counter).
+template <int NT, bool COUNT>
 __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 {
     extern __shared__ uint4 rsm[];
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     const uint64_t total = (uint64_t)P.nsweeps * 2;
     const size_t side_words = (size_t)(h >> 1) * 32 * Kg;   // u64 per side
     uint64_t done = 0;
+    uint32_t nflip = 0;   // accepted flips of this thread's owned sites
     int cyc = 0, buf = 0;
     // the next density sample: sweeps s (counted after the sweep, 1-based)
     // with s >= burn and (s - burn) % stride == 0, tracked incrementally
@@ -261,6 +265,7 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 FL0[buf * nt + tid] = f0;
                 FL1[buf * nt + tid] = f1;
                 HB[buf * nt + tid] = b0 | (b1 << 1);
+                if (COUNT && owned) nflip += popc4(f0) + popc4(f1);
                 if (ip < hc || done + hc < total) {
                     o0 = philox10(grp0, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
                     o1 = philox10(grp1, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
@@ -430,6 +435,7 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
         }
         ++cyc;
     }
+    if (COUNT && nflip) atomicAdd(P.flips, (unsigned long long)nflip);
     if (owned) {
         uint32_t* b0 = P.rows0 + (int64_t)y0 * RW + k0;
         __stcg(reinterpret_cast<uint4*>(b0), He0);
@@ -446,10 +452,13 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     }
 }
 
-static const void* reg_pick(int threads)
+static const void* reg_pick(int threads, bool count = false)
 {
-    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512>)
-                         : reinterpret_cast<const void*>(&regdom_kernel<256>);
+    if (count)
+        return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, true>)
+                             : reinterpret_cast<const void*>(&regdom_kernel<256, true>);
+    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, false>)
+                         : reinterpret_cast<const void*>(&regdom_kernel<256, false>);
 }
 
 size_t regdom_smem_bytes(int threads, int max_local_pairs)
@@ -468,6 +477,8 @@ int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm)
     *blocks_per_sm = 0;
     const void* k = reg_pick(threads);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reg_pick(threads, true), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return (int)e;
@@ -479,9 +490,10 @@ int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm)
 
 int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t sweep0, uint32_t nsweeps,
                   const DevRng& rng, unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                  uint32_t stride, const uint8_t* colours, void* stream)
+                  uint32_t stride, const uint8_t* colours, unsigned long long* flips, void* stream)
 {
     RegParams P;
+    P.flips = flips;
     P.rows0 = rows + g.row_words;
     P.g = g;
     P.stripe_lo = plan.stripe_lo;
@@ -499,7 +511,7 @@ int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t s
     P.stride = stride;
     P.epoch = epoch;
     void* args[] = {&P};
-    return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads), dim3(plan.ctas), dim3(plan.threads), args,
+    return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads, flips != nullptr), dim3(plan.ctas), dim3(plan.threads), args,
                                             plan.smem_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 

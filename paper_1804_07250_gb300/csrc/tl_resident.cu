@@ -50,6 +50,7 @@ struct ResParams {
     uint64_t burn;
     uint32_t stride;
     unsigned int epoch;
+    unsigned long long* flips;  // accepted-flip counter, or nullptr
 };
 
 TL_DEV uint64_t globaltimer()
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         const uint64_t first = (uint64_t)P.sweep0 + 1;
         next_sample = first <= P.burn ? P.burn : P.burn + ((first - P.burn + P.stride - 1) / P.stride) * P.stride;
     }
+    uint32_t nflip = 0;   // accepted flips of this thread's owned sites
     uint32_t cyc_sweep = P.sweep0, cyc_pass = 0;   // first pass of the current cycle
     // pass table of a cycle: item range, random-plane offset, pass slot |
     // colour << 8, sweep.  The slot keys the random numbers, the colour (the
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     const uint32_t onext = (fi.y >> 31) ? rbuf[e.z + it + 1].x : 0u;
                     r[q] = domino_fast_compute(sm + fi.x, RW, g.K, (int)((pass + (uint32_t)y) & 1u), m << 2,
                                                rbuf[e.z + it], onext);
+                    if (y >= lo && y < hi) nflip += r[q].nfl;
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(HALF) : "memory");
 #pragma unroll
@@ -318,8 +321,11 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                     const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
                     const RndPre rnd{rbuf + e.z + it, P.npre, cap, RndPhilox{grp, sweep, slot, P.rng}};
+                    // a six-vertex face row y touches vertex rows y and y + 1
+                    // and is this stripe's if its lower row is
                     group_update<LAT, TK>(srow0 + (int64_t)y * RW, RW, g, y, m, pass, rnd, P.th,
-                                          LAT == LAT_SIXV ? s_ttab : nullptr, ctab);
+                                          LAT == LAT_SIXV ? s_ttab : nullptr, ctab,
+                                          (P.flips && y >= lo && y < hi) ? &nflip : nullptr);
                 }
             } else if (i + 1 < hc) {
                 gen(i + 1);
@@ -448,6 +454,7 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         ++cyc;
     }
     copy_rows_to_global(P.rows0 + (int64_t)lo * RW, srow0 + (int64_t)lo * RW, (int64_t)(hi - lo) * RW, tid, NT);
+    if (P.flips && nflip) atomicAdd(P.flips, (unsigned long long)nflip);
 }
 
 template <int LAT, int TK>
@@ -486,9 +493,10 @@ int resident_prepare(const Geom& g, int thr_kind, int threads, bool fast, size_t
 int launch_resident(const Geom& g, uint32_t* rows, const ResidentPlan& plan, uint32_t sweep0,
                     uint32_t nsweeps, const DevRng& rng, const ThrView& th, const int2* grange,
                     unsigned int epoch, unsigned long long* ring, uint32_t* counts, uint64_t burn,
-                    uint32_t stride, const uint8_t* colours, void* stream)
+                    uint32_t stride, const uint8_t* colours, unsigned long long* flips, void* stream)
 {
     ResParams P;
+    P.flips = flips;
     P.rows0 = rows + g.row_words;
     P.g = g;
     P.stripe_lo = plan.stripe_lo;

@@ -105,3 +105,31 @@ def test_batch_autotune_keeps_results(T, ctx):
     for c, r in zip(chains, ref):
         r.run(20)
         assert c.state_hash() == r.state_hash()
+
+
+def test_autotune_cache(T, ctx):
+    # a second batch with the same key (lattices, threshold kinds, rows to a
+    # power of two, SMs) takes the cached plan without trials
+    import time
+
+    import torch
+    T.Batch.autotune_cache_clear()
+    specs = _specs()
+    stream = torch.cuda.Stream()
+    b1 = T.Batch(ctx, [_make(T, ctx, sp, 700 + i) for i, sp in enumerate(specs)])
+    t0 = time.perf_counter()
+    p1 = b1.autotune(trial_sweeps=16, stream=stream)
+    first = time.perf_counter() - t0
+    chains = [_make(T, ctx, sp, 800 + i) for i, sp in enumerate(specs)]
+    b2 = T.Batch(ctx, chains)
+    t0 = time.perf_counter()
+    p2 = b2.autotune(trial_sweeps=16, stream=stream)
+    second = time.perf_counter() - t0
+    assert (p2["tile_rows"], p2["sweeps_per_launch"]) == (p1["tile_rows"], p1["sweeps_per_launch"])
+    assert second < first / 4
+    assert all(c.sweep == 0 for c in chains)
+    b2.run(12, stream=stream)
+    stream.synchronize()
+    for i, (sp, c) in enumerate(zip(specs, chains)):
+        assert np.array_equal(c.read_state(), _oracle(sp, 800 + i, 12))
+    T.Batch.autotune_cache_clear()
