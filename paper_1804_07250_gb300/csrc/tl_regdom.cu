@@ -129,7 +129,6 @@ template <int NT, bool COUNT>
 __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 {
     extern __shared__ uint4 rsm[];
-    __shared__ int s_ok;
     __shared__ unsigned long long s_red[NT / 32];
     const int nt = blockDim.x;
     uint4* FL0 = rsm;                                        // [2][nt] flips of row y0 (for the pair below)
@@ -360,46 +359,45 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
         }
         int ok = 1;
         if (act && !owned) {
-            // halo pair: poll the neighbour's published words, one row at a time
+            // halo pair: poll the neighbour's published words (both rows at
+            // once); the random words of the next pass, which halo items
+            // skipped at the end of the cycle, are drawn while the first
+            // loads are in flight
             const bool below = y0 < lo;
             const int idx = below ? (y0 - (lo - h)) >> 1 : (y0 - hi) >> 1;
             const unsigned long long* src = P.xbuf +
                                             ((size_t)((below ? c - 1 : c + 1) * 2 + par) * 2 + (below ? 1 : 0)) *
                                                 side_words +
                                             (size_t)idx * 32 * Kg;
+            unsigned long long a[16], b[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &a[q], &b[q]);
+            o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+            o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
             const uint64_t t_wait = rd_globaltimer();
-            PairWords pw;
+            unsigned need = 0xFFFFu;
+            while (true) {
 #pragma unroll
-            for (int r = 0; r < 2 && ok; ++r) {
-                unsigned long long a[8], b[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) rd_ld2(src + ((size_t)(8 * r + q) * Kg + m) * 2, &a[q], &b[q]);
-                unsigned need = 0xFFu;
-                while (true) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if ((need >> q & 1u) && (a[q] & 0xFFFFFFFF00000000ull) == tag &&
-                            (b[q] & 0xFFFFFFFF00000000ull) == tag)
-                            need &= ~(1u << q);
-                    if (!need) break;
-                    if (*(volatile int*)P.status || rd_globaltimer() - t_wait > kRegWaitLimitNs) {
-                        atomicExch(P.status, 1);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (need >> q & 1u) rd_ld2(src + ((size_t)(8 * r + q) * Kg + m) * 2, &a[q], &b[q]);
+                for (int q = 0; q < 16; ++q)
+                    if ((need >> q & 1u) && (a[q] & 0xFFFFFFFF00000000ull) == tag &&
+                        (b[q] & 0xFFFFFFFF00000000ull) == tag)
+                        need &= ~(1u << q);
+                if (!need) break;
+                if (*(volatile int*)P.status || rd_globaltimer() - t_wait > kRegWaitLimitNs) {
+                    atomicExch(P.status, 1);
+                    ok = 0;
+                    break;
                 }
+                __nanosleep(32);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    pw.v[4 * r + q] = make_uint4((uint32_t)a[2 * q], (uint32_t)b[2 * q], (uint32_t)a[2 * q + 1],
-                                                 (uint32_t)b[2 * q + 1]);
+                for (int q = 0; q < 16; ++q)
+                    if (need >> q & 1u) rd_ld2(src + ((size_t)q * Kg + m) * 2, &a[q], &b[q]);
             }
             if (ok) {
-                He0 = pw.v[0]; Ho0 = pw.v[1]; Ve0 = pw.v[2]; Vo0 = pw.v[3];
-                He1 = pw.v[4]; Ho1 = pw.v[5]; Ve1 = pw.v[6]; Vo1 = pw.v[7];
+#define TL_RG_W(q) make_uint4((uint32_t)a[2 * (q)], (uint32_t)b[2 * (q)], (uint32_t)a[2 * (q) + 1], (uint32_t)b[2 * (q) + 1])
+                He0 = TL_RG_W(0); Ho0 = TL_RG_W(1); Ve0 = TL_RG_W(2); Vo0 = TL_RG_W(3);
+                He1 = TL_RG_W(4); Ho1 = TL_RG_W(5); Ve1 = TL_RG_W(6); Vo1 = TL_RG_W(7);
+#undef TL_RG_W
             }
         }
         // copies of the row below (Vt) and of the left group's odd-Hz top
@@ -411,11 +409,8 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
         }
         // a status word raised anywhere (a wait that gave up in another CTA,
         // or raised by the host) ends every CTA at its next exchange
-        if (tid == 0) s_ok = *(volatile int*)P.status ? 0 : 1;
-        __syncthreads();
-        if (!ok) s_ok = 0;
-        __syncthreads();
-        if (!s_ok) return;   // the state is undefined; the host reports TL_ETIMEOUT
+        if (tid == 0 && *(volatile int*)P.status) ok = 0;
+        if (!__syncthreads_and(ok)) return;   // the state is undefined; the host reports TL_ETIMEOUT
         if (act) {
             if (ib >= 0) {
                 Se = RV[2 * ib];
@@ -425,12 +420,6 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 const uint2 r = RH[il];
                 pv0 = r.x;
                 pv1 = r.y;
-            }
-            if (!owned) {
-                // halo items skipped the end of the cycle: their next random
-                // words were not drawn
-                o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
-                o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
             }
         }
         ++cyc;
