@@ -29,6 +29,7 @@
 #include "tl_device.cuh"
 
 #include <cstdint>
+#include <type_traits>
 
 namespace tl {
 
@@ -124,8 +125,10 @@ struct PairWords {
 };
 
 // COUNT: the chain counts its accepted flips (a separate instantiation, so
-// the default path carries no counter).
-template <int NT, bool COUNT>
+// the default path carries no counter).  RND: the colour of every pass slot
+// comes from the host's table (random order) instead of slot s updating
+// colour s.
+template <int NT, bool COUNT, bool RND>
 __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 {
     extern __shared__ uint4 rsm[];
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     const size_t side_words = (size_t)(h >> 1) * 32 * Kg;   // u64 per side
     uint64_t done = 0;
     uint32_t nflip = 0;   // accepted flips of this thread's owned sites
-    int cyc = 0, buf = 0;
+    int cyc = 0;
     // the next density sample: sweeps s (counted after the sweep, 1-based)
     // with s >= burn and (s - burn) % stride == 0, tracked incrementally
     uint64_t next_sample = ~0ull;
@@ -235,104 +238,126 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
         const uint64_t first = (uint64_t)P.sweep0 + 1;
         next_sample = first <= P.burn ? P.burn : P.burn + ((first - P.burn + P.stride - 1) / P.stride) * P.stride;
     }
-    uint32_t sweep = P.sweep0, slot = 0;
-    // random words of the next pass, computed before the barrier of the
-    // current one (they depend on no state)
-    uint4 o0 = {}, o1 = {};
+    uint32_t sweep = P.sweep0;
+    // Random words, ping-pong by pass slot: the words of slot s are in
+    // oS0 / oS1 (rows y0, y0 + 1).  A pass draws the next pass's words in
+    // the same block as its own update (independent chains, interleaved);
+    // they depend on no state.  Every exchange cycle has an even number of
+    // passes, so cycles (and launches) start at slot 0 and the shared-memory
+    // buffer of a pass is its slot.
+    uint4 oA0 = {}, oA1 = {}, oB0 = {}, oB1 = {};
     if (act) {
-        o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
-        o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+        oA0 = philox10(grp0, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
+        oA1 = philox10(grp1, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
     }
-    while (true) {
-        const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
-        for (int ip = 1; ip <= hc; ++ip) {
-            const uint32_t col = P.colours ? (uint32_t)P.colours[(size_t)(sweep - P.sweep0) * 2 + slot] : slot;
-            const bool par1 = (col & 1u) != 0;   // parity of row y0 (y0 is even)
-            const bool live = act && (dist + ip <= h);
-            // the next pass slot
-            const uint32_t nslot = slot ^ 1u, nsweep = slot ? sweep + 1 : sweep;
-            if (live) {
-                uint4 f0, f1;
-                uint32_t b0, b1;
-                if (!par1) {
-                    f0 = row_par0(He0, Ho0, pv0, Ve0, Se, o0, b0);
-                    f1 = row_par1(He1, Ho1, Vo1, Vo0, o1, b1);
-                } else {
-                    f0 = row_par1(He0, Ho0, Vo0, So, o0, b0);
-                    f1 = row_par0(He1, Ho1, pv1, Ve1, Ve0, o1, b1);
-                }
-                FL0[buf * nt + tid] = f0;
-                FL1[buf * nt + tid] = f1;
-                HB[buf * nt + tid] = b0 | (b1 << 1);
-                if (COUNT && owned) nflip += popc4(f0) + popc4(f1);
-                if (ip < hc || done + hc < total) {
-                    o0 = philox10(grp0, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
-                    o1 = philox10(grp1, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
-                }
+    // One pass: colour parity PAR1 (the parity of row y0, y0 even), slot SL.
+    auto pass = [&](auto par1c, auto slc, int ip, const uint4& oc0, const uint4& oc1, uint4& on0, uint4& on1) {
+        constexpr bool par1 = decltype(par1c)::value;
+        constexpr int sl = decltype(slc)::value;
+        const bool live = act && (dist + ip <= h);
+        const uint32_t nslot = sl ^ 1, nsweep = sl ? sweep + 1 : sweep;
+        uint4* const fl0 = FL0 + sl * nt;
+        uint4* const fl1 = FL1 + sl * nt;
+        uint32_t* const hb = HB + sl * nt;
+        if (live) {
+            uint4 f0, f1;
+            uint32_t b0, b1;
+            on0 = philox10(grp0, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
+            on1 = philox10(grp1, nsweep, nslot, P.rng.stream, P.rng.k0, P.rng.k1);
+            if (!par1) {
+                f0 = row_par0(He0, Ho0, pv0, Ve0, Se, oc0, b0);
+                f1 = row_par1(He1, Ho1, Vo1, Vo0, oc1, b1);
+            } else {
+                f0 = row_par1(He0, Ho0, Vo0, So, oc0, b0);
+                f1 = row_par0(He1, Ho1, pv1, Ve1, Ve0, oc1, b1);
             }
-            __syncthreads();
-            if (live) {
-                // the pair below flipped its upper row (Vt row y0-1 at the
-                // other parity); the pair above its lower row (Vt row y0+1 at
-                // this parity); left / right groups their boundary bits
-                const uint4 zb = make_uint4(0u, 0u, 0u, 0u);
-                const uint4 fb = ib >= 0 ? FL1[buf * nt + ib] : zb;
-                const uint4 fa = ia >= 0 ? FL0[buf * nt + ia] : zb;
-                const uint32_t hl = il >= 0 ? HB[buf * nt + il] : 0u;
-                const uint32_t hr = ir >= 0 ? HB[buf * nt + ir] : 0u;
-                if (!par1) {
-                    So = x4(So, fb);
-                    Ve1 = x4(Ve1, fa);
-                    Ho0.w ^= (hr & 1u) << 31;          // right group's first site, row y0
-                    pv1 ^= ((hl >> 1) & 1u) << 31;     // left group's last site, row y0+1
-                } else {
-                    Se = x4(Se, fb);
-                    Vo1 = x4(Vo1, fa);
-                    pv0 ^= (hl & 1u) << 31;            // left group's last site, row y0
-                    Ho1.w ^= ((hr >> 1) & 1u) << 31;   // right group's first site, row y0+1
-                }
+            fl0[tid] = f0;
+            fl1[tid] = f1;
+            hb[tid] = b0 | (b1 << 1);
+            if (COUNT && owned) nflip += popc4(f0) + popc4(f1);
+        }
+        __syncthreads();
+        if (live) {
+            // the pair below flipped its upper row (Vt row y0-1 at the
+            // other parity); the pair above its lower row (Vt row y0+1 at
+            // this parity); left / right groups their boundary bits
+            const uint4 zb = make_uint4(0u, 0u, 0u, 0u);
+            const uint4 fb = ib >= 0 ? fl1[ib] : zb;
+            const uint4 fa = ia >= 0 ? fl0[ia] : zb;
+            const uint32_t hl = il >= 0 ? hb[il] : 0u;
+            const uint32_t hr = ir >= 0 ? hb[ir] : 0u;
+            if (!par1) {
+                So = x4(So, fb);
+                Ve1 = x4(Ve1, fa);
+                Ho0.w ^= (hr & 1u) << 31;          // right group's first site, row y0
+                pv1 ^= ((hl >> 1) & 1u) << 31;     // left group's last site, row y0+1
+            } else {
+                Se = x4(Se, fb);
+                Vo1 = x4(Vo1, fa);
+                pv0 ^= (hl & 1u) << 31;            // left group's last site, row y0
+                Ho1.w ^= ((hr >> 1) & 1u) << 31;   // right group's first site, row y0+1
             }
-            buf ^= 1;
-            if (slot == 1u) {
-                // end of a sweep: owned rows are exact
-                const bool sample = (uint64_t)sweep + 1 == next_sample;
-                if (sample) next_sample += P.stride;
-                if (P.ring || sample) {
-                    uint64_t acc = 0;
-                    if (owned) {
-                        const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+        }
+        if constexpr (sl == 1) {
+            // end of a sweep: owned rows are exact
+            const bool sample = (uint64_t)sweep + 1 == next_sample;
+            if (sample) next_sample += P.stride;
+            if (P.ring || sample) {
+                uint64_t acc = 0;
+                if (owned) {
+                    const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
 #pragma unroll
-                        for (int r = 0; r < 2; ++r) {
-                            const int y = y0 + r;
-                            if (y >= g.H) continue;
+                    for (int r = 0; r < 2; ++r) {
+                        const int y = y0 + r;
+                        if (y >= g.H) continue;
 #pragma unroll
-                            for (int pl = 0; pl < 4; ++pl) {
-                                const uint4 v4 = pw.v[4 * r + pl];
-                                if (sample && any4(v4))
-                                    word_count_sliced4(v4, (int64_t)y * RW + (int64_t)pl * K + k0,
-                                                       (int64_t)g.H * RW, P.counts);
-                                if (!P.ring) continue;
-                                const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                        for (int pl = 0; pl < 4; ++pl) {
+                            const uint4 v4 = pw.v[4 * r + pl];
+                            if (sample && any4(v4))
+                                word_count_sliced4(v4, (int64_t)y * RW + (int64_t)pl * K + k0,
+                                                   (int64_t)g.H * RW, P.counts);
+                            if (!P.ring) continue;
+                            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                                for (int w = 0; w < 4; ++w)
-                                    if (vv[w]) acc += word_hash(vv[w], g, y, pl, k0 + w);
-                            }
+                            for (int w = 0; w < 4; ++w)
+                                if (vv[w]) acc += word_hash(vv[w], g, y, pl, k0 + w);
                         }
                     }
-                    if (P.ring) {
-                        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
-                        if ((tid & 31) == 0) s_red[tid >> 5] = acc;
-                        __syncthreads();
-                        if (tid == 0) {
-                            unsigned long long t = 0;
-                            for (int wv = 0; wv < (nt + 31) / 32; ++wv) t += s_red[wv];
-                            atomicAdd(P.ring + (sweep - P.sweep0), t);
-                        }
+                }
+                if (P.ring) {
+                    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+                    if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+                    __syncthreads();
+                    if (tid == 0) {
+                        unsigned long long t = 0;
+                        for (int wv = 0; wv < (nt + 31) / 32; ++wv) t += s_red[wv];
+                        atomicAdd(P.ring + (sweep - P.sweep0), t);
                     }
                 }
             }
             sweep = nsweep;
-            slot = nslot;
+        }
+    };
+    using F = std::integral_constant<bool, false>;
+    using Tr = std::integral_constant<bool, true>;
+    using S0 = std::integral_constant<int, 0>;
+    using S1 = std::integral_constant<int, 1>;
+    while (true) {
+        const int hc = (int)((total - done) < (uint64_t)h ? (total - done) : (uint64_t)h);
+        for (int ip = 1; ip <= hc; ip += 2) {
+            if constexpr (!RND) {
+                // fixed order: slot s updates colour s
+                pass(F{}, S0{}, ip, oA0, oA1, oB0, oB1);
+                pass(Tr{}, S1{}, ip + 1, oB0, oB1, oA0, oA1);
+            } else {
+                // random order: the colour of each slot from the host's table
+                const uint8_t* cs = P.colours + (size_t)(sweep - P.sweep0) * 2;
+                const bool p0 = (cs[0] & 1u) != 0, p1 = (cs[1] & 1u) != 0;
+                if (p0) pass(Tr{}, S0{}, ip, oA0, oA1, oB0, oB1);
+                else pass(F{}, S0{}, ip, oA0, oA1, oB0, oB1);
+                if (p1) pass(Tr{}, S1{}, ip + 1, oB0, oB1, oA0, oA1);
+                else pass(F{}, S1{}, ip + 1, oB0, oB1, oA0, oA1);
+            }
         }
         done += (uint64_t)hc;
         if (done >= total) break;
@@ -372,8 +397,8 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
             unsigned long long a[16], b[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &a[q], &b[q]);
-            o0 = philox10(grp0, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
-            o1 = philox10(grp1, sweep, slot, P.rng.stream, P.rng.k0, P.rng.k1);
+            oA0 = philox10(grp0, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
+            oA1 = philox10(grp1, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
             const uint64_t t_wait = rd_globaltimer();
             unsigned need = 0xFFFFu;
             while (true) {
@@ -441,13 +466,17 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     }
 }
 
-static const void* reg_pick(int threads, bool count = false)
+template <bool COUNT, bool RND>
+static const void* reg_pick_nt(int threads)
 {
-    if (count)
-        return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, true>)
-                             : reinterpret_cast<const void*>(&regdom_kernel<256, true>);
-    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, false>)
-                         : reinterpret_cast<const void*>(&regdom_kernel<256, false>);
+    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, COUNT, RND>)
+                         : reinterpret_cast<const void*>(&regdom_kernel<256, COUNT, RND>);
+}
+
+static const void* reg_pick(int threads, bool count, bool rnd)
+{
+    if (count) return rnd ? reg_pick_nt<true, true>(threads) : reg_pick_nt<true, false>(threads);
+    return rnd ? reg_pick_nt<false, true>(threads) : reg_pick_nt<false, false>(threads);
 }
 
 size_t regdom_smem_bytes(int threads, int max_local_pairs)
@@ -464,10 +493,11 @@ size_t regdom_smem_bytes(int threads, int max_local_pairs)
 int regdom_prepare(int threads, size_t smem_bytes, int* blocks_per_sm)
 {
     *blocks_per_sm = 0;
-    const void* k = reg_pick(threads);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reg_pick(threads, true), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    const void* k = reg_pick(threads, false, false);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v)
+        e = cudaFuncSetAttribute(reg_pick(threads, (v & 1) != 0, (v & 2) != 0),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return (int)e;
@@ -500,7 +530,7 @@ int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t s
     P.stride = stride;
     P.epoch = epoch;
     void* args[] = {&P};
-    return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads, flips != nullptr), dim3(plan.ctas), dim3(plan.threads), args,
+    return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads, flips != nullptr, colours != nullptr), dim3(plan.ctas), dim3(plan.threads), args,
                                             plan.smem_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
