@@ -469,8 +469,9 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 template <bool COUNT, bool RND>
 static const void* reg_pick_nt(int threads)
 {
-    return threads > 256 ? reinterpret_cast<const void*>(&regdom_kernel<512, COUNT, RND>)
-                         : reinterpret_cast<const void*>(&regdom_kernel<256, COUNT, RND>);
+    if (threads > 384) return reinterpret_cast<const void*>(&regdom_kernel<512, COUNT, RND>);
+    if (threads > 256) return reinterpret_cast<const void*>(&regdom_kernel<384, COUNT, RND>);
+    return reinterpret_cast<const void*>(&regdom_kernel<256, COUNT, RND>);
 }
 
 static const void* reg_pick(int threads, bool count, bool rnd)
