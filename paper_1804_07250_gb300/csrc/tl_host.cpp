@@ -1733,6 +1733,13 @@ static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void*
             if (ec) return fail(TL_ECUDA, "colour kernel: %s", cudaGetErrorString((cudaError_t)ec));
             c->launches += 1;
         }
+        if (c->use_reg && (uint64_t)n * c->g.passes > (uint64_t)c->reg.halo) {
+            // the register kernel's exchange tags count cycles within one
+            // launch: its buffers start every launch cleared
+            CUDA_TRY(cudaMemsetAsync(c->xbuf_d, 0,
+                                     (size_t)c->reg.ctas * 4 * c->reg.halo * c->g.row_words * sizeof(unsigned long long),
+                                     SS(stream)));
+        }
         const int e =
             c->use_reg
                 ? launch_regdom(c->g, c->rows, c->reg, (uint32_t)c->sweep, (uint32_t)n, c->rng, ++c->epoch,

@@ -23,9 +23,10 @@
 // Between CTAs the stripes exchange boundary rows every `halo` passes (the
 // halo rows are recomputed redundantly, the exact region shrinking by one
 // row per pass; rows whose results can no longer reach the owned stripe are
-// skipped).  Boundary words travel as 64-bit words tagged with (launch
-// epoch, cycle), double buffered by cycle parity; every wait is bounded
-// (2 s) and raises a status word instead of hanging.
+// skipped).  Boundary rows travel packed in 64-bit words of 61 data bits
+// and a 3-bit cycle tag, double buffered by cycle parity (the buffers are
+// cleared before every launch); every wait is bounded (2 s) and raises a
+// status word instead of hanging.
 #include "tl_device.cuh"
 
 #include <cstdint>
@@ -123,6 +124,35 @@ TL_DEV uint4 row_par1(uint4& He, uint4& Ho, uint4& N, uint4& S, uint4 o, uint32_
 struct PairWords {
     uint4 v[8];
 };
+
+// Exchange format: the pair's 1,024 state bits (the 32 words above, word j
+// holding stream bits [32j, 32j + 32)) in 17 fields of 61 bits, each field
+// in the low bits of a 64-bit word whose top 3 bits carry the cycle tag;
+// field 17 carries the tag alone.  Nine 16-byte units per pair and group
+// instead of sixteen 32-bit words each with a 32-bit tag.  A 64-bit access
+// is single-copy atomic, so a field whose tag is current holds current data.
+constexpr int kXFields = 18, kXUnits = 9;
+constexpr unsigned long long kXMask = (1ull << 61) - 1;
+
+TL_DEV unsigned long long pack61(const uint32_t (&w)[32], int i)
+{
+    const int lo = 61 * i;
+    if (lo >= 1024) return 0ull;
+    const int wi = lo >> 5, s = lo & 31;
+    unsigned long long x = (unsigned long long)w[wi] >> s;
+    if (wi + 1 < 32) x |= (unsigned long long)w[wi + 1] << (32 - s);
+    if (s > 3 && wi + 2 < 32) x |= (unsigned long long)w[wi + 2] << (64 - s);
+    return x & kXMask;
+}
+
+// word j of the stream from fields with their tags cleared
+TL_DEV uint32_t unpack61(const unsigned long long (&f)[kXFields], int j)
+{
+    const int lo = 32 * j, i0 = lo / 61, o = lo - 61 * i0;
+    unsigned long long x = f[i0] >> o;
+    if (61 - o < 32) x |= f[i0 + 1] << (61 - o);
+    return (uint32_t)x;
+}
 
 // COUNT: the chain counts its accepted flips (a separate instantiation, so
 // the default path carries no counter).  RND: the colour of every pass slot
@@ -364,10 +394,22 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
 
         // ---- exchange of boundary rows with the neighbouring stripes ----
         const int par = cyc & 1;
-        const unsigned long long tag =
-            ((unsigned long long)(((P.epoch & 0xFFFFu) << 16) | (unsigned)((cyc + 1) & 0xFFFF))) << 32;
+        // the buffer of a cycle parity holds the data of cycle cyc - 2, or
+        // zeros (cleared before every launch): a tag of cyc mod 4, plus one,
+        // tells them apart
+        const unsigned long long tag = (unsigned long long)((cyc & 3) + 1) << 61;
         if (owned) {
-            const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+            uint32_t w[32];
+            {
+                const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    w[4 * v] = pw.v[v].x;
+                    w[4 * v + 1] = pw.v[v].y;
+                    w[4 * v + 2] = pw.v[v].z;
+                    w[4 * v + 3] = pw.v[v].w;
+                }
+            }
             for (int s = 0; s < 2; ++s) {
                 const bool pub = s == 0 ? (!bot && y0 < lo + h) : (!top && y0 >= hi - h);
                 if (!pub) continue;
@@ -375,11 +417,8 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 unsigned long long* dst = P.xbuf + ((size_t)(c * 2 + par) * 2 + s) * side_words +
                                           (size_t)idx * 32 * Kg;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {   // 16-byte unit u: words 2u, 2u + 1 of the pair
-                    const uint4 v = pw.v[u >> 1];
-                    const uint32_t a = (u & 1) ? v.z : v.x, b = (u & 1) ? v.w : v.y;
-                    rd_st2(dst + ((size_t)u * Kg + m) * 2, tag | a, tag | b);
-                }
+                for (int u = 0; u < kXUnits; ++u)   // 16-byte unit u: fields 2u, 2u + 1
+                    rd_st2(dst + ((size_t)u * Kg + m) * 2, tag | pack61(w, 2 * u), tag | pack61(w, 2 * u + 1));
             }
         }
         int ok = 1;
@@ -394,18 +433,17 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                                             ((size_t)((below ? c - 1 : c + 1) * 2 + par) * 2 + (below ? 1 : 0)) *
                                                 side_words +
                                             (size_t)idx * 32 * Kg;
-            unsigned long long a[16], b[16];
+            unsigned long long f[kXFields];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &a[q], &b[q]);
+            for (int q = 0; q < kXUnits; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &f[2 * q], &f[2 * q + 1]);
             oA0 = philox10(grp0, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
             oA1 = philox10(grp1, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
             const uint64_t t_wait = rd_globaltimer();
-            unsigned need = 0xFFFFu;
+            unsigned need = (1u << kXUnits) - 1;
             while (true) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if ((need >> q & 1u) && (a[q] & 0xFFFFFFFF00000000ull) == tag &&
-                        (b[q] & 0xFFFFFFFF00000000ull) == tag)
+                for (int q = 0; q < kXUnits; ++q)
+                    if ((need >> q & 1u) && (f[2 * q] & ~kXMask) == tag && (f[2 * q + 1] & ~kXMask) == tag)
                         need &= ~(1u << q);
                 if (!need) break;
                 if (*(volatile int*)P.status || rd_globaltimer() - t_wait > kRegWaitLimitNs) {
@@ -415,11 +453,13 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 }
                 __nanosleep(32);
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (need >> q & 1u) rd_ld2(src + ((size_t)q * Kg + m) * 2, &a[q], &b[q]);
+                for (int q = 0; q < kXUnits; ++q)
+                    if (need >> q & 1u) rd_ld2(src + ((size_t)q * Kg + m) * 2, &f[2 * q], &f[2 * q + 1]);
             }
             if (ok) {
-#define TL_RG_W(q) make_uint4((uint32_t)a[2 * (q)], (uint32_t)b[2 * (q)], (uint32_t)a[2 * (q) + 1], (uint32_t)b[2 * (q) + 1])
+#pragma unroll
+                for (int q = 0; q < kXFields; ++q) f[q] &= kXMask;
+#define TL_RG_W(v) make_uint4(unpack61(f, 4 * (v)), unpack61(f, 4 * (v) + 1), unpack61(f, 4 * (v) + 2), unpack61(f, 4 * (v) + 3))
                 He0 = TL_RG_W(0); Ho0 = TL_RG_W(1); Ve0 = TL_RG_W(2); Vo0 = TL_RG_W(3);
                 He1 = TL_RG_W(4); Ho1 = TL_RG_W(5); Ve1 = TL_RG_W(6); Vo1 = TL_RG_W(7);
 #undef TL_RG_W
