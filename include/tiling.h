@@ -507,6 +507,28 @@ typedef struct tl_batch tl_batch;
  * runs on the per-pass kernel (it has no waits). */
 int tl_debug_raise_status(tl_chain* c, tl_batch* b);
 
+/* Bounds-checked build (no counterpart in the paper): libtiling_debug.so,
+ * built with -DTL_DEBUG (`python paper_1804_07250_gb300/_build.py --debug`),
+ * checks the computed indices of the kernels' shared-memory and global
+ * accesses (the register and shared-memory resident kernels, the batched
+ * kernel, the per-pass and read-back kernels, domino shuffling).  An index
+ * outside its buffer is counted and the access skipped, so a wrong index
+ * becomes a reported failure instead of a fault; results with no failure
+ * are those of the normal build.
+ *  tl_debug_build:    1 in the checked build, 0 in the normal one.
+ *  tl_debug_checks:   waits for the device, then reports the failed checks
+ *                     of every kernel file since the last clear: their count
+ *                     (`failures`), and the id, index and bound of the first
+ *                     (each pointer may be NULL); clears them if `clear`.
+ *                     TL_EUNSUPPORTED in the normal build.
+ *  tl_debug_selftest: runs one check of an index out of its range (index 5,
+ *                     bound 3, id 999) whose access is skipped; a following
+ *                     tl_debug_checks reports it.  TL_EUNSUPPORTED in the
+ *                     normal build. */
+int tl_debug_build(void);
+int tl_debug_checks(int clear, uint64_t* failures, int* first_id, int64_t* index, int64_t* bound);
+int tl_debug_selftest(void);
+
 typedef struct {
     int tile_rows;          /* rows per tile (0 = keep) */
     int sweeps_per_launch;  /* R (0 = keep) */

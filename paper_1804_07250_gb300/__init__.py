@@ -18,11 +18,14 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtiling.so")
+# TL_DEBUG=1 selects the bounds-checked build (_build.py --debug)
+DEBUG_BUILD = os.environ.get("TL_DEBUG") == "1"
+LIB_PATH = os.path.join(_HERE, "libtiling_debug.so" if DEBUG_BUILD else "libtiling.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libtiling.so is missing: build it with "
-                      "`python paper_1804_07250_gb300/_build.py` (needs nvcc)")
+    raise ImportError("%s is missing: build it with "
+                      "`python paper_1804_07250_gb300/_build.py%s` (needs nvcc)"
+                      % (os.path.basename(LIB_PATH), " --debug" if DEBUG_BUILD else ""))
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -112,6 +115,9 @@ _SIG = {
     "tl_chain_get_plan": (_i, [_vp, ctypes.POINTER(Plan)]),
     "tl_chain_sync": (_i, [_vp, _vp]),
     "tl_debug_raise_status": (_i, [_vp, _vp]),
+    "tl_debug_build": (_i, []),
+    "tl_debug_checks": (_i, [ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tl_debug_selftest": (_i, []),
     "tl_checkpoint": (_i, [_vp, _vp]),
     "tl_autotune_cache_clear": (None, []),
     "tl_chain_count_flips": (_i, [_vp, ctypes.c_int]),
@@ -152,6 +158,28 @@ EXPORTED = tuple(_SIG)
 
 def lib():
     return _lib
+
+
+def debug_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(_lib.tl_debug_build())
+
+
+def debug_checks(clear: bool = True) -> dict:
+    """Failed bounds checks of the checked build since the last clear
+    (tl_debug_checks): count, and id / index / bound of the first."""
+    n = _u64(0)
+    fid = ctypes.c_int(0)
+    ix = ctypes.c_int64(0)
+    bd = ctypes.c_int64(0)
+    _check(_lib.tl_debug_checks(1 if clear else 0, ctypes.byref(n), ctypes.byref(fid), ctypes.byref(ix),
+                                ctypes.byref(bd)))
+    return {"failures": int(n.value), "id": fid.value, "index": ix.value, "bound": bd.value}
+
+
+def debug_selftest():
+    """Run one out-of-range check whose access is skipped (tl_debug_selftest)."""
+    _check(_lib.tl_debug_selftest())
 
 
 def _check(rc):

@@ -17,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtiling.so")
+# the bounds-checked build (-DTL_DEBUG): the binding loads it when TL_DEBUG=1
+LIB_DEBUG = os.path.join(HERE, "libtiling_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tl_kernels.cu", "tl_resident.cu", "tl_regdom.cu", "tl_batch.cu", "tl_shuffle.cu", "tl_host.cpp", "tl_thurston.cpp"]
@@ -29,8 +31,8 @@ def nvcc() -> str:
     return cand
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
            "-Xcompiler", "-fPIC,-fvisibility=hidden", "-Xptxas", "-warn-spills",
            "-c", os.path.join(CSRC, src), "-o", obj, *extra]
@@ -38,30 +40,35 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tiling.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, debug: bool = False) -> str:
+    """Build libtiling.so, or with `debug` the bounds-checked
+    libtiling_debug.so (-DTL_DEBUG, objects in _build/debug)."""
+    lib = LIB_DEBUG if debug else LIB
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    if debug:
+        extra += ["-DTL_DEBUG"]
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
+    tmp = lib + ".tmp.%d" % os.getpid()
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
     subprocess.run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                     "-Xlinker", "-rpath," + cuda_lib], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -147,6 +147,14 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchChain* __restr
         const bool bot_x = slo == -1, top_x = shi == g.H + 1;
         const uint32_t* srcp = ch.rows[src] + RW;   // global row 0
         uint32_t* dstp = ch.rows[src ^ 1] + RW;
+#ifdef TL_DEBUG
+        {
+            // the tile and its halo rows fit the block's shared memory
+            uint32_t dyn;
+            asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+            if (!TL_IN((int64_t)(shi - slo) * RW * 4 - 1, (int64_t)dyn, 301)) continue;
+        }
+#endif
         // the tile and its halo rows are contiguous: one bulk copy into shared
         // memory (rows are whole 16-byte units, buffers 256-byte aligned)
         if (threadIdx.x == 0) bulk_load(sm, srcp + (int64_t)slo * RW, (uint32_t)((int64_t)(shi - slo) * RW * 4), &s_bar);
@@ -282,6 +290,19 @@ int launch_batch_copy(const BatchChain* chains, const BatchTile* tiles, int ntil
     batch_copy_kernel<<<grid > 0 ? grid : 1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles,
                                                                                              from);
     return (int)cudaGetLastError();
+}
+
+// This file's debug word (failures, then the id, index and bound of the
+// first failed check); cudaErrorNotSupported in the normal build.
+int dbg_fetch_batch(unsigned long long* out, bool clear)
+{
+#ifdef TL_DEBUG
+    return tl_dbg_fetch(out, clear);
+#else
+    (void)out;
+    (void)clear;
+    return (int)cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace tl

@@ -11,6 +11,41 @@ namespace tl {
 
 #define TL_DEV __device__ __forceinline__
 
+// Bounds checks of the debug build (-DTL_DEBUG, libtiling_debug.so).  Each
+// checked access asks TL_IN(i, n, id) first: an index outside [0, n) is
+// counted in this translation unit's debug word (failures, then the id,
+// index and bound of the first) and the access is skipped, so a wrong index
+// shows up as a reported failure (tl_debug_checks) instead of a fault.  In
+// the normal build the checks compile to nothing.  The ids name the check
+// sites: 1xx register kernel, 2xx shared-memory resident kernel, 3xx batch
+// kernel, 4xx per-pass and read-back kernels, 5xx domino shuffling.
+#ifdef TL_DEBUG
+static __device__ unsigned long long tl_dbg_word[4];
+__device__ __noinline__ static bool tl_dbg_fail(long long i, long long n, int id)
+{
+    if (atomicAdd(&tl_dbg_word[0], 1ull) == 0ull) {
+        tl_dbg_word[1] = (unsigned long long)id;
+        tl_dbg_word[2] = (unsigned long long)i;
+        tl_dbg_word[3] = (unsigned long long)n;
+    }
+    return false;
+}
+TL_DEV bool tl_in(long long i, long long n, int id) { return (i >= 0 && i < n) ? true : tl_dbg_fail(i, n, id); }
+#define TL_IN(i, n, id) ::tl::tl_in((long long)(i), (long long)(n), (id))
+// host side: read (and clear) this translation unit's word
+static inline int tl_dbg_fetch(unsigned long long* out, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, tl_dbg_word, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess && clear) {
+        const unsigned long long z[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(tl_dbg_word, z, sizeof(z));
+    }
+    return (int)e;
+}
+#else
+#define TL_IN(i, n, id) true
+#endif
+
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplications by fixed odd constants, XOR of the high halves
 // into the other two words and the round key, and a Weyl key schedule.
@@ -582,6 +617,9 @@ TL_DEV void word_count_sliced(uint32_t w, int64_t i, int64_t plane_words, uint32
 // per four words instead of per word.
 TL_DEV void word_count_sliced4(uint4 w, int64_t i, int64_t plane_words, uint32_t* cplanes)
 {
+#ifdef TL_DEBUG
+    if (!TL_IN(i + 3, plane_words, 107)) return;
+#endif
     uint4 carry = w;
     for (int b = 0; b < 32 && any4(carry); ++b) {
         uint4* p = reinterpret_cast<uint4*>(cplanes + (int64_t)b * plane_words + i);

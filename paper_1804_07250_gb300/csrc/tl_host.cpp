@@ -1814,6 +1814,61 @@ TL_API int tl_chain_sync(tl_chain* c, void* stream)
 
 static int batch_raise_status(tl_batch* b);
 
+TL_API int tl_debug_build(void)
+{
+#ifdef TL_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+TL_API int tl_debug_checks(int clear, uint64_t* failures, int* first_id, int64_t* index, int64_t* bound)
+{
+#ifdef TL_DEBUG
+    CUDA_TRY(cudaDeviceSynchronize());
+    int (*const fetch[])(unsigned long long*, bool) = {dbg_fetch_kernels, dbg_fetch_regdom, dbg_fetch_resident,
+                                                       dbg_fetch_batch, dbg_fetch_shuffle};
+    uint64_t n = 0;
+    int id = 0;
+    int64_t ix = 0, bd = 0;
+    for (auto f : fetch) {
+        unsigned long long w[4] = {0, 0, 0, 0};
+        const int e = f(w, clear != 0);
+        if (e) return fail(TL_ECUDA, "tl_debug_checks: %s", cudaGetErrorString((cudaError_t)e));
+        if (w[0] && !n) {
+            id = (int)w[1];
+            ix = (int64_t)w[2];
+            bd = (int64_t)w[3];
+        }
+        n += w[0];
+    }
+    if (failures) *failures = n;
+    if (first_id) *first_id = id;
+    if (index) *index = ix;
+    if (bound) *bound = bd;
+    return TL_OK;
+#else
+    (void)clear;
+    (void)failures;
+    (void)first_id;
+    (void)index;
+    (void)bound;
+    return fail(TL_EUNSUPPORTED, "tl_debug_checks: not the checked build (build with --debug, load with TL_DEBUG=1)");
+#endif
+}
+
+TL_API int tl_debug_selftest(void)
+{
+#ifdef TL_DEBUG
+    const int e = dbg_selftest();
+    if (e) return fail(TL_ECUDA, "tl_debug_selftest: %s", cudaGetErrorString((cudaError_t)e));
+    return TL_OK;
+#else
+    return fail(TL_EUNSUPPORTED, "tl_debug_selftest: not the checked build");
+#endif
+}
+
 TL_API int tl_debug_raise_status(tl_chain* c, tl_batch* b)
 {
     if (!c && !b) return fail(TL_EINVAL, "tl_debug_raise_status: NULL argument");

@@ -178,4 +178,15 @@ int launch_batch_hash(const BatchChain* chains, const BatchTile* tiles, int ntil
                       unsigned long long* out, void* stream);
 int launch_batch_copy(const BatchChain* chains, const BatchTile* tiles, int ntiles, int from, void* stream);
 
+// Debug words of the kernel files (debug build, -DTL_DEBUG): failures, then
+// the id, index and bound of the first failed bounds check; each returns
+// cudaErrorNotSupported in the normal build.  dbg_selftest runs one check
+// on an out-of-range index (id 999) without the access it guards.
+int dbg_fetch_kernels(unsigned long long* out, bool clear);
+int dbg_fetch_regdom(unsigned long long* out, bool clear);
+int dbg_fetch_resident(unsigned long long* out, bool clear);
+int dbg_fetch_batch(unsigned long long* out, bool clear);
+int dbg_fetch_shuffle(unsigned long long* out, bool clear);
+int dbg_selftest();
+
 }  // namespace tl

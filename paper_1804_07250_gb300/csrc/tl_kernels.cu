@@ -47,8 +47,14 @@ __global__ void __launch_bounds__(256) pass_global_kernel(uint32_t* __restrict__
         y = rix;
         rr = y;
     }
+#ifdef TL_DEBUG
+    if (!TL_IN(y, g.H, 401)) return;
+#endif
     const int2 gr = grange[y];
     if (m < gr.x || m >= gr.y) return;
+#ifdef TL_DEBUG
+    if (!TL_IN(4 * m + 3, g.K, 402)) return;
+#endif
     const uint32_t grp = (uint32_t)(rr * g.Kg + m);
     uint32_t* row = rows0 + (int64_t)y * g.row_words;
     const RndPhilox rnd{grp, sweep, slot, rng};
@@ -354,6 +360,10 @@ __global__ void __launch_bounds__(256) height_seg_kernel(const uint32_t* __restr
 {
     const int* sg = seg + 6 * (size_t)blockIdx.x;
     const int y = sg[0], lo = sg[1], hi = sg[2];
+#ifdef TL_DEBUG
+    // a segment of row y spans vertices lo .. hi of a row of hw heights
+    if (!(TL_IN(y, g.H, 403) && TL_IN(lo, hw, 404) && TL_IN(hi, hw, 404))) return;
+#endif
     int32_t* o = out + (size_t)y * hw;
     __shared__ int part[256];
     const int n = hi - lo + 1;
@@ -564,6 +574,47 @@ int launch_height_noalloc(const Geom& g, const uint32_t* rows, const int* seg, i
     const int e = noalloc_scratch(device, &base);
     if (e) return e;
     return launch_height(g, rows, seg, nseg, hw, hh, out, base, stream);
+}
+
+// This file's debug word (failures, then the id, index and bound of the
+// first failed check); cudaErrorNotSupported in the normal build.
+int dbg_fetch_kernels(unsigned long long* out, bool clear)
+{
+#ifdef TL_DEBUG
+    return tl_dbg_fetch(out, clear);
+#else
+    (void)out;
+    (void)clear;
+    return (int)cudaErrorNotSupported;
+#endif
+}
+
+#ifdef TL_DEBUG
+// One check on an index out of its range (5 of 3, id 999) and none of the
+// access it guards: the failure must be recorded, nothing else happens.
+__global__ void dbg_selftest_kernel(int* out)
+{
+    int x = 0;
+    if (TL_IN(threadIdx.x + 5, 3, 999)) x = 1;
+    out[threadIdx.x] = x;
+}
+#endif
+
+int dbg_selftest()
+{
+#ifdef TL_DEBUG
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e == cudaSuccess) {
+        dbg_selftest_kernel<<<1, 1>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d);
+    return (int)e;
+#else
+    return (int)cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace tl

@@ -219,6 +219,12 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
             const int2 ha = s_hull[pi + 1];
             if (m >= ha.x && m < ha.y) ia = s_off[pi + 1] + (m - ha.x);
         }
+#ifdef TL_DEBUG
+        if (ib >= 0 && !TL_IN(ib, nt, 101)) ib = -1;
+        if (ia >= 0 && !TL_IN(ia, nt, 102)) ia = -1;
+        if (il >= 0 && !TL_IN(il, nt, 103)) il = -1;
+        if (ir >= 0 && !TL_IN(ir, nt, 104)) ir = -1;
+#endif
     }
     const int y0 = slo + 2 * pi;
     const bool owned = act && y0 >= lo && y0 < hi;
@@ -234,7 +240,14 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
     uint4 He0 = {}, Ho0 = {}, Ve0 = {}, Vo0 = {}, He1 = {}, Ho1 = {}, Ve1 = {}, Vo1 = {}, Se = {}, So = {};
     uint32_t pv0 = 0, pv1 = 0;
     const int k0 = 4 * m;
-    if (act) {
+    // rows y0 - 1 .. y0 + 1 of the padded buffer (rows -1 .. H) and words
+    // k0 .. k0 + 3 of a plane row
+#ifdef TL_DEBUG
+    const bool inb = TL_IN(y0 + 1, g.H + 1, 105) && TL_IN(k0 + 3, K, 106);
+#else
+    constexpr bool inb = true;
+#endif
+    if (act && inb) {
         const uint32_t* b0 = P.rows0 + (int64_t)y0 * RW + k0;
         const uint32_t* b1 = b0 + RW;
         const uint32_t* bs = b0 - RW;
@@ -361,7 +374,10 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                     if (tid == 0) {
                         unsigned long long t = 0;
                         for (int wv = 0; wv < (nt + 31) / 32; ++wv) t += s_red[wv];
-                        atomicAdd(P.ring + (sweep - P.sweep0), t);
+#ifdef TL_DEBUG
+                        if (TL_IN(sweep - P.sweep0, P.nsweeps, 110))
+#endif
+                            atomicAdd(P.ring + (sweep - P.sweep0), t);
                     }
                 }
             }
@@ -414,6 +430,12 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 const bool pub = s == 0 ? (!bot && y0 < lo + h) : (!top && y0 >= hi - h);
                 if (!pub) continue;
                 const int idx = s == 0 ? (y0 - lo) >> 1 : (y0 - (hi - h)) >> 1;
+#ifdef TL_DEBUG
+                if (!TL_IN(((size_t)(c * 2 + par) * 2 + s) * side_words + (size_t)idx * 32 * Kg +
+                               ((size_t)(kXUnits - 1) * Kg + m) * 2 + 1,
+                           (size_t)C * 4 * side_words, 108))
+                    continue;
+#endif
                 unsigned long long* dst = P.xbuf + ((size_t)(c * 2 + par) * 2 + s) * side_words +
                                           (size_t)idx * 32 * Kg;
 #pragma unroll
@@ -434,8 +456,19 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                                                 side_words +
                                             (size_t)idx * 32 * Kg;
             unsigned long long f[kXFields];
+#ifdef TL_DEBUG
+            if (!TL_IN(((size_t)((below ? c - 1 : c + 1) * 2 + par) * 2 + (below ? 1 : 0)) * side_words +
+                           (size_t)idx * 32 * Kg + ((size_t)(kXUnits - 1) * Kg + m) * 2 + 1,
+                       (size_t)C * 4 * side_words, 109)) {
+                atomicExch(P.status, 1);   // reported as a failed wait; nothing is read
+                ok = 0;
+            }
 #pragma unroll
-            for (int q = 0; q < kXUnits; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &f[2 * q], &f[2 * q + 1]);
+            for (int q = 0; q < kXFields; ++q) f[q] = 0ull;
+            if (ok)
+#endif
+#pragma unroll
+                for (int q = 0; q < kXUnits; ++q) rd_ld2(src + ((size_t)q * Kg + m) * 2, &f[2 * q], &f[2 * q + 1]);
             oA0 = philox10(grp0, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
             oA1 = philox10(grp1, sweep, 0u, P.rng.stream, P.rng.k0, P.rng.k1);
             const uint64_t t_wait = rd_globaltimer();
@@ -490,7 +523,7 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
         ++cyc;
     }
     if (COUNT && nflip) atomicAdd(P.flips, (unsigned long long)nflip);
-    if (owned) {
+    if (owned && inb) {
         uint32_t* b0 = P.rows0 + (int64_t)y0 * RW + k0;
         __stcg(reinterpret_cast<uint4*>(b0), He0);
         __stcg(reinterpret_cast<uint4*>(b0 + K), Ho0);
@@ -573,6 +606,19 @@ int launch_regdom(const Geom& g, uint32_t* rows, const RegPlan& plan, uint32_t s
     void* args[] = {&P};
     return (int)cudaLaunchCooperativeKernel(reg_pick(plan.threads, flips != nullptr, colours != nullptr), dim3(plan.ctas), dim3(plan.threads), args,
                                             plan.smem_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// This file's debug word (failures, then the id, index and bound of the
+// first failed check); cudaErrorNotSupported in the normal build.
+int dbg_fetch_regdom(unsigned long long* out, bool clear)
+{
+#ifdef TL_DEBUG
+    return tl_dbg_fetch(out, clear);
+#else
+    (void)out;
+    (void)clear;
+    return (int)cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace tl

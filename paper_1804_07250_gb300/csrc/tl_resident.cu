@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
             const int2 gr = P.grange[y];
             int o = off[t * (nloc + 1) + r];
             for (int m = gr.x; m < gr.y; ++m) {
+#ifdef TL_DEBUG
+                if (!TL_IN(o, P.cap_items, 201)) break;
+#endif
                 if (FAST) {
                     // word offset of (row y, plane 0, word 4m) and whether m+1 follows in this row
                     fitems[o] = make_uint2((uint32_t)((int64_t)r * RW + 4 * m),
@@ -265,6 +268,9 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
         const int4 e = s_ptab[i];
         const uint32_t sweep = s_psweep[i], pass = (uint32_t)e.w & 255u;   // slot
         for (int it = rtid; it < e.y; it += HALF) {
+#ifdef TL_DEBUG
+            if (!TL_IN(e.x + it, P.cap_items, 202) || !TL_IN(e.z + it, cap, 203)) continue;
+#endif
             const uint32_t item = items[e.x + it];
             const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
             const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
@@ -302,9 +308,20 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                 for (int q = 0; q < MAXI; ++q) {
                     const int it = rtid + q * HALF;
                     has[q] = it < e.y;
+#ifdef TL_DEBUG
+                    if (has[q] && !(TL_IN(e.x + it, P.cap_items, 204) && TL_IN(e.z + it + 1, cap + 1, 205)))
+                        has[q] = false;
+#endif
                     if (!has[q]) continue;
                     // {smem word offset of (y, k0), y | m << 16 | next-adjacent << 31}
                     const uint2 fi = fitems[e.x + it];
+#ifdef TL_DEBUG
+                    // the update reads rows y - 1 and y of the local rows
+                    if (!TL_IN((int64_t)fi.x - RW, (int64_t)(nloc - 1) * RW, 206)) {
+                        has[q] = false;
+                        continue;
+                    }
+#endif
                     const int y = (int)(fi.y & 0xFFFFu), m = (int)((fi.y >> 16) & 0xFFu);
                     const uint32_t onext = (fi.y >> 31) ? rbuf[e.z + it + 1].x : 0u;
                     r[q] = domino_fast_compute(sm + fi.x, RW, g.K, (int)((pass + (uint32_t)y) & 1u), m << 2,
@@ -317,6 +334,12 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                     if (has[q]) domino_fast_store(r[q]);
             } else if (!FAST && upd_role) {
                 for (int it = rtid; it < e.y; it += HALF) {
+#ifdef TL_DEBUG
+                    if (!TL_IN(e.x + it, P.cap_items, 207) || !TL_IN(e.z + it, cap, 203)) continue;
+                    // dominoes and lozenges read rows y - 1 and y, a six-vertex
+                    // face row the vertex rows y and y + 1
+                    if (!TL_IN((int)(items[e.x + it] >> 8) - (LAT == LAT_SIXV ? 0 : 1), nloc - 1, 208)) continue;
+#endif
                     const uint32_t item = items[e.x + it];
                     const int y = slo + (int)(item >> 8), m = (int)(item & 255u);
                     const uint32_t grp = (uint32_t)(((LAT == LAT_SIXV) ? (y >> 1) : y) * g.Kg + m);
@@ -357,7 +380,10 @@ __global__ void __launch_bounds__(NT, 1) resident_kernel(const ResParams P)
                         if (tid == 0) {
                             unsigned long long t = 0;
                             for (int wv = 0; wv < NT / 32; ++wv) t += s_red[wv];
-                            atomicAdd(P.ring + (sweep - P.sweep0), t);
+#ifdef TL_DEBUG
+                            if (TL_IN(sweep - P.sweep0, P.nsweeps, 209))
+#endif
+                                atomicAdd(P.ring + (sweep - P.sweep0), t);
                         }
                     }
                     __syncthreads();
@@ -540,6 +566,19 @@ int launch_slot_colours(uint8_t* out, uint32_t sweep0, uint32_t nsweeps, int pas
     slot_colours_kernel<<<(unsigned)(blocks < 1024 ? (blocks ? blocks : 1) : 1024), 256, 0,
                           reinterpret_cast<cudaStream_t>(stream)>>>(out, sweep0, nsweeps, passes, rng);
     return (int)cudaGetLastError();
+}
+
+// This file's debug word (failures, then the id, index and bound of the
+// first failed check); cudaErrorNotSupported in the normal build.
+int dbg_fetch_resident(unsigned long long* out, bool clear)
+{
+#ifdef TL_DEBUG
+    return tl_dbg_fetch(out, clear);
+#else
+    (void)out;
+    (void)clear;
+    return (int)cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace tl

@@ -80,6 +80,10 @@ __global__ void shuffle_move_kernel(const uint8_t* __restrict__ A, uint8_t* __re
     int wi, y;
     if (!row_word(n, K, wi, y)) return;
     const int r = y + n;
+#ifdef TL_DEBUG
+    // the word written: row r of 2n cell rows, bytes 4 wi .. 4 wi + 3 of a pitch-S row
+    if (!(TL_IN(r, 2 * n, 501) && TL_IN(4 * wi + 3, S, 502))) return;
+#endif
     uint8_t cw[3][6];
     load_window(A, n, S, r, wi, cw);
     uint32_t outw = 0;
@@ -131,6 +135,9 @@ __global__ void shuffle_fill_kernel(const uint8_t* __restrict__ B, uint8_t* __re
     int wi, y;
     if (!row_word(n, K, wi, y)) return;
     const int r = y + n;
+#ifdef TL_DEBUG
+    if (!(TL_IN(r, 2 * n, 503) && TL_IN(4 * wi + 3, S, 504))) return;
+#endif
     const uint32_t bw = word_at(B, n, S, r, wi);
     uint32_t outw = bw;
     bool any = false;
@@ -221,6 +228,19 @@ int launch_shuffle(int n, uint8_t* A, uint8_t* B, uint8_t* F, const DevRng* rng,
     }
     shuffle_canon_kernel<<<grid_for_cells((int64_t)4 * n * n), 256, 0, s>>>(cur, n, canon);
     return (int)cudaGetLastError();
+}
+
+// This file's debug word (failures, then the id, index and bound of the
+// first failed check); cudaErrorNotSupported in the normal build.
+int dbg_fetch_shuffle(unsigned long long* out, bool clear)
+{
+#ifdef TL_DEBUG
+    return tl_dbg_fetch(out, clear);
+#else
+    (void)out;
+    (void)clear;
+    return (int)cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace tl

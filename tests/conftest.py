@@ -18,3 +18,17 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checks(request):
+    # Under the bounds-checked build (TL_DEBUG=1) every GPU test must leave
+    # no failed index check behind.
+    yield
+    if os.environ.get("TL_DEBUG") == "1" and request.node.get_closest_marker("gpu"):
+        import torch
+        if not torch.cuda.is_available():
+            return
+        import paper_1804_07250_gb300 as T
+        r = T.debug_checks(clear=True)
+        assert r["failures"] == 0, "failed bounds checks: %s" % r
