@@ -347,11 +347,16 @@ def run_ours(args):
     traffic = recorded_traffic(wl["name"], ksrc, {"kernel": plan["kernel"]}) if plan["kernel"] in RESIDENT_KERNELS \
         else None
 
-    # end to end through the C-ABI with host buffers
-    init_host = dom.initial_state()
-    h_out = np.empty(hshape, dtype=np.int32)
-    s_out = np.empty(dom.canon_shape, dtype=np.uint8)
-    n_out = np.empty((4, info.height - 1, info.width - 1), dtype=np.float64) if density else None
+    # end to end through the C-ABI with host buffers (page-locked, as a
+    # caller streaming states in and results out would hold them)
+    def pinned(shape, dtype):
+        return torch.empty(tuple(shape), dtype=dtype, pin_memory=True).numpy()
+
+    init_host = pinned(dom.canon_shape, torch.uint8)
+    init_host[...] = dom.initial_state()
+    h_out = pinned(hshape, torch.int32)
+    s_out = pinned(dom.canon_shape, torch.uint8)
+    n_out = pinned((4, info.height - 1, info.width - 1), torch.float64) if density else None
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     barrier()

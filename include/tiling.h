@@ -384,7 +384,12 @@ int tl_run_sweeps_hashed(tl_chain* c, uint64_t k, uint64_t* ring, void* stream);
 int tl_read_state(tl_chain* c, uint8_t* canon, size_t cap, void* stream);
 
 /* Replace the chain's state (host or device canonical buffer, n ==
- * canon_bytes).  The configuration is validated as in tl_chain_create. */
+ * canon_bytes).  The configuration is validated as in tl_chain_create (every
+ * byte 0 or 1; every face covered once, or the six-vertex boundary and ice
+ * rule), on the device: host bytes are first copied into the chain's
+ * scratch.  TL_EINVAL names the first failure and leaves the chain's state
+ * unchanged.  Returns once the check is done (the caller's buffer may then
+ * be reused); the packing is enqueued on `stream`. */
 int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* stream);
 
 /* Order-independent state hash: sum mod 2^64 over set canonical bits i of

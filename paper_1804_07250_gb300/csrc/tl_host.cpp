@@ -998,6 +998,13 @@ struct tl_chain {
     bool use_reg = false;
     RegPlan reg{};
     int2* hull_d = nullptr;
+    // device validation of written states: the domain's cover or boundary
+    // edges, and the first failure found
+    uint8_t* vaux_d = nullptr;
+    unsigned long long* vfirst_d = nullptr;
+    // device staging of density read-backs to host memory (grown on demand)
+    double* dscratch = nullptr;
+    size_t dscratch_n = 0;
 };
 
 static void chain_free(tl_chain* c)
@@ -1020,6 +1027,9 @@ static void chain_free(tl_chain* c)
     cudaFree(c->status_d);
     cudaFree(c->hull_d);
     cudaFree(c->flips_d);
+    cudaFree(c->vaux_d);
+    cudaFree(c->vfirst_d);
+    cudaFree(c->dscratch);
     tl_ctx* ctx = c->ctx;
     delete c;
     ctx_release(ctx);
@@ -1946,6 +1956,55 @@ TL_API int tl_read_state(tl_chain* c, uint8_t* canon, size_t cap, void* stream)
     return TL_OK;
 }
 
+// Checks the canonical state `dcanon` (device memory) against the chain's
+// domain on the device; the same checks, and an error naming the first
+// failure, as the host validation.
+static int validate_device(tl_chain* c, const uint8_t* dcanon, void* stream)
+{
+    const tl_domain& d = c->dom_copy;
+    const Geom& g = c->g;
+    if (!c->vaux_d) {
+        std::vector<uint8_t> aux;
+        if (g.lattice == LAT_SIXV) {
+            const int N = g.N;
+            aux.resize((size_t)4 * N);
+            for (int k = 1; k <= N; ++k) {
+                aux[k - 1] = d.init[(size_t)k * g.W];
+                aux[N + k - 1] = d.init[(size_t)k * g.W + N];
+                aux[2 * N + k - 1] = d.init[(size_t)g.W * g.H + k];
+                aux[3 * N + k - 1] = d.init[(size_t)g.W * g.H + (size_t)N * g.W + k];
+            }
+        } else {
+            aux = d.cover;
+        }
+        TL_TRY(dev_alloc(&c->vaux_d, aux.size(), "validation data"));
+        CUDA_TRY(cudaMemcpy(c->vaux_d, aux.data(), aux.size(), cudaMemcpyHostToDevice));
+    }
+    if (!c->vfirst_d) TL_TRY(dev_alloc(&c->vfirst_d, 1, "validation result"));
+    const int e = launch_validate(g, dcanon, c->vaux_d, c->vfirst_d, stream);
+    if (e) return fail(TL_ECUDA, "validation kernels: %s", cudaGetErrorString((cudaError_t)e));
+    c->launches += 2;
+    unsigned long long first = 0;
+    CUDA_TRY(cudaMemcpyAsync(&first, c->vfirst_d, sizeof(first), cudaMemcpyDeviceToHost, SS(stream)));
+    CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    if (first == ~0ull) return TL_OK;
+    const int kind = (int)(first >> 48);
+    const long long pos = (long long)(first & ((1ull << 48) - 1));
+    switch (kind) {
+    case 1: return fail(TL_EINVAL, "state byte %lld is not 0 or 1", pos);
+    case 2:
+    case 3: return fail(TL_EINVAL, "domino: edge outside the box set");
+    case 4:
+        return fail(TL_EINVAL, "domino: face (%lld,%lld) not covered once", pos % (g.W - 1), pos / (g.W - 1));
+    case 5:
+        return fail(TL_EINVAL, "lozenge: triangles at (%lld,%lld) not covered once", pos % (g.W + 1) - 1,
+                    pos / (g.W + 1) - 1);
+    case 6: return fail(TL_EINVAL, "six-vertex: bit set off the lattice at (%lld,%lld)", pos % g.W, pos / g.W);
+    case 7: return fail(TL_EINVAL, "six-vertex: external edges differ from the boundary");
+    default: return fail(TL_EINVAL, "six-vertex: ice rule fails at (%lld,%lld)", pos % g.W, pos / g.W);
+    }
+}
+
 TL_API int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* stream)
 {
     if (!c || !canon) return fail(TL_EINVAL, "tl_write_state: NULL argument");
@@ -1954,17 +2013,18 @@ TL_API int tl_write_state(tl_chain* c, const uint8_t* canon, size_t n, void* str
     CUDA_TRY(cudaSetDevice(c->ctx->device));
     TL_TRY(require_local(canon, c->ctx->device, "tl_write_state"));
     const bool dev = is_device_ptr(canon);
-    std::vector<uint8_t> host;
-    const uint8_t* check = canon;
     if (dev) {
-        host.resize(n);
-        CUDA_TRY(cudaStreamSynchronize(SS(stream)));
-        CUDA_TRY(cudaMemcpy(host.data(), canon, n, cudaMemcpyDeviceToHost));
-        check = host.data();
+        // checked where it is, then copied and packed
+        TL_TRY(validate_device(c, canon, stream));
+        return upload_state(c, canon, true, stream);
     }
-    TL_TRY(validate(&c->dom_copy, check));
-    TL_TRY(upload_state(c, canon, dev, stream));
-    if (!dev) CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+    // host bytes: copied into the chain's unpacked scratch, checked there on
+    // the device, packed only if valid (the chain's state is untouched
+    // otherwise)
+    CUDA_TRY(cudaMemcpyAsync(c->canon, canon, n, cudaMemcpyHostToDevice, SS(stream)));
+    TL_TRY(validate_device(c, c->canon, stream));
+    CUDA_TRY(launch_pack(c->g, c->canon, c->rows, stream));
+    c->launches += 1;
     return TL_OK;
 }
 
@@ -2363,13 +2423,18 @@ static int to_output(tl_chain* c, double* out, size_t n, void* stream, F launch)
         c->launches += 1;
         return TL_OK;
     }
-    double* tmp = nullptr;
-    TL_TRY(dev_alloc(&tmp, n, "density output"));
-    int e = launch(tmp);
+    if (c->dscratch_n < n) {
+        CUDA_TRY(cudaStreamSynchronize(SS(stream)));
+        cudaFree(c->dscratch);
+        c->dscratch = nullptr;
+        c->dscratch_n = 0;
+        TL_TRY(dev_alloc(&c->dscratch, n, "density output"));
+        c->dscratch_n = n;
+    }
+    int e = launch(c->dscratch);
     c->launches += 1;
-    if (!e) e = cudaMemcpyAsync(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, SS(stream));
+    if (!e) e = cudaMemcpyAsync(out, c->dscratch, n * sizeof(double), cudaMemcpyDeviceToHost, SS(stream));
     if (!e) e = cudaStreamSynchronize(SS(stream));
-    cudaFree(tmp);
     if (e) return fail(TL_ECUDA, "density readback: %s", cudaGetErrorString((cudaError_t)e));
     return TL_OK;
 }

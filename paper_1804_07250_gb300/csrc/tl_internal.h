@@ -178,6 +178,11 @@ int launch_batch_hash(const BatchChain* chains, const BatchTile* tiles, int ntil
                       unsigned long long* out, void* stream);
 int launch_batch_copy(const BatchChain* chains, const BatchTile* tiles, int ntiles, int from, void* stream);
 
+// Validation of a canonical state on the device (tl_kernels.cu): *first is
+// ~0 if valid, else (kind << 48 | position) of the first failure; `aux` is
+// the domain's cover (dominoes, lozenges) or boundary edges (six-vertex).
+int launch_validate(const Geom& g, const uint8_t* canon, const uint8_t* aux, unsigned long long* first, void* stream);
+
 // Debug words of the kernel files (debug build, -DTL_DEBUG): failures, then
 // the id, index and bound of the first failed bounds check; each returns
 // cudaErrorNotSupported in the normal build.  dbg_selftest runs one check

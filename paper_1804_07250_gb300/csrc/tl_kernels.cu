@@ -184,6 +184,122 @@ int launch_threshold_planes(const Geom& g, const uint32_t* t_site_dev, uint32_t*
 }
 
 // ---------------------------------------------------------------------------
+// Validation of a canonical state against its domain, on the device: every
+// byte 0 or 1; dominoes: no edge outside the box, every face of the domain
+// covered once and no other; lozenges: every triangle covered as the domain
+// says; six-vertex: no bit off the lattice, the external edges those of the
+// boundary, the ice rule at every vertex.  The first failure in the order of
+// a row-major scan (kinds in this order) is kept as the smallest code
+// (kind << 48 | position) by an atomic min; *first stays ~0 if the state is
+// valid.  Kinds: 1 byte (position = byte index), 2 domino edge right of the
+// box (y), 3 domino edge above the box (x), 4 domino face (y (W-1) + x),
+// 5 lozenge triangles ((y+1)(W+1) + x+1), 6 six-vertex bit off the lattice
+// (Y W + X), 7 six-vertex boundary (k), 8 six-vertex ice rule (Y W + X).
+// ---------------------------------------------------------------------------
+struct DevCanon {
+    const uint8_t* s;
+    int W, H;
+    TL_DEV int at(int type, int x, int y) const
+    {
+        if (x < 0 || y < 0 || x >= W || y >= H) return 0;
+        return s[((size_t)type * H + y) * W + x];
+    }
+};
+
+TL_DEV void vfail(unsigned long long* first, int kind, uint64_t pos)
+{
+    atomicMin(first, ((unsigned long long)kind << 48) | (unsigned long long)pos);
+}
+
+__global__ void validate_bytes_kernel(const uint8_t* __restrict__ s, size_t n, unsigned long long* first)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (s[i] > 1) vfail(first, 1, i);
+}
+
+// aux: face cover [(H-1)][(W-1)]
+__global__ void validate_domino_kernel(const uint8_t* __restrict__ s, Geom g, const uint8_t* __restrict__ cover,
+                                       unsigned long long* first)
+{
+    const DevCanon c{s, g.W, g.H};
+    const int64_t nf = (int64_t)(g.W - 1) * (g.H - 1);
+    const int64_t nall = nf + g.H + g.W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nall; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < g.H) {
+            if (c.at(0, g.W - 1, (int)i)) vfail(first, 2, (uint64_t)i);
+        } else if (i < g.H + g.W) {
+            if (c.at(1, (int)(i - g.H), g.H - 1)) vfail(first, 3, (uint64_t)(i - g.H));
+        } else {
+            const int64_t f = i - g.H - g.W;
+            const int y = (int)(f / (g.W - 1)), x = (int)(f - (int64_t)y * (g.W - 1));
+            const int k = c.at(0, x, y) + c.at(0, x, y + 1) + c.at(1, x, y) + c.at(1, x + 1, y);
+            if (k != cover[f]) vfail(first, 4, (uint64_t)f);
+        }
+    }
+}
+
+// aux: triangle cover, up then down, [(H+1)][(W+1)] each
+__global__ void validate_lozenge_kernel(const uint8_t* __restrict__ s, Geom g, const uint8_t* __restrict__ cover,
+                                        unsigned long long* first)
+{
+    const DevCanon c{s, g.W, g.H};
+    const int TW = g.W + 1, TH = g.H + 1;
+    const int64_t nt = (int64_t)TW * TH;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / TW) - 1, x = (int)(i % TW) - 1;
+        const int u = c.at(0, x, y) + c.at(1, x + 1, y) + c.at(2, x, y);
+        const int v = c.at(2, x, y) + c.at(1, x, y) + c.at(0, x, y + 1);
+        if (u != cover[i] || v != cover[nt + i]) vfail(first, 5, (uint64_t)i);
+    }
+}
+
+// aux: the boundary edges of the domain, [4][N]: for k = 1..N (index k - 1)
+// type 0 at (0, k), type 0 at (N, k), type 1 at (k, 0), type 1 at (k, N)
+__global__ void validate_sixv_kernel(const uint8_t* __restrict__ s, Geom g, const uint8_t* __restrict__ bnd,
+                                     unsigned long long* first)
+{
+    const DevCanon c{s, g.W, g.H};
+    const int N = g.N;
+    const int64_t nb = (int64_t)g.W * g.H;
+    const int64_t nall = nb + N + nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nall; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nb) {
+            const int Y = (int)(i / g.W), X = (int)(i % g.W);
+            const bool hreal = Y >= 1 && Y <= N && X <= N;
+            const bool vreal = X >= 1 && X <= N && Y <= N;
+            if ((c.at(0, X, Y) && !hreal) || (c.at(1, X, Y) && !vreal)) vfail(first, 6, (uint64_t)i);
+        } else if (i < nb + N) {
+            const int k = (int)(i - nb) + 1;
+            if (c.at(0, 0, k) != bnd[k - 1] || c.at(0, N, k) != bnd[N + k - 1] || c.at(1, k, 0) != bnd[2 * N + k - 1] ||
+                c.at(1, k, N) != bnd[3 * N + k - 1])
+                vfail(first, 7, (uint64_t)k);
+        } else {
+            const int64_t j = i - nb - N;
+            const int Y = (int)(j / g.W), X = (int)(j % g.W);
+            if (Y < 1 || Y > N || X < 1 || X > N) continue;
+            const int L = c.at(0, X - 1, Y), R = c.at(0, X, Y), D = c.at(1, X, Y - 1), U = c.at(1, X, Y);
+            if (L + U != D + R) vfail(first, 8, (uint64_t)j);
+        }
+    }
+}
+
+int launch_validate(const Geom& g, const uint8_t* canon, const uint8_t* aux, unsigned long long* first, void* stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(first, 0xFF, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return (int)e;
+    const size_t n = (size_t)g.ntype * g.W * g.H;
+    validate_bytes_kernel<<<grid_for((int64_t)n, 256), 256, 0, st>>>(canon, n, first);
+    if (g.lattice == LAT_DOMINO)
+        validate_domino_kernel<<<grid_for((int64_t)(g.W - 1) * (g.H - 1) + g.W + g.H, 256), 256, 0, st>>>(canon, g, aux, first);
+    else if (g.lattice == LAT_LOZENGE)
+        validate_lozenge_kernel<<<grid_for((int64_t)(g.W + 1) * (g.H + 1), 256), 256, 0, st>>>(canon, g, aux, first);
+    else
+        validate_sixv_kernel<<<grid_for((int64_t)2 * g.W * g.H + g.N, 256), 256, 0, st>>>(canon, g, aux, first);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Observables.
 // ---------------------------------------------------------------------------
 __global__ void hash_kernel(const uint32_t* __restrict__ rows0, Geom g, unsigned long long* out)

@@ -368,3 +368,46 @@ def test_density_counts_many_samples(T, ctx, kind, args, kernel):
         O.accumulate(st, counts)
     assert samples == 300
     assert np.array_equal(np.rint(dens * 300).astype(np.uint32), counts)
+
+
+def _reject(T, ch, bad):
+    with pytest.raises(T.TilingError) as e:
+        ch.write_state(bad)
+    assert e.value.code == T.TL_EINVAL
+    return str(e.value)
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_write_state_rejects_every_kind(T, ctx, where):
+    # the device validation rejects what the host validation of
+    # tl_chain_create rejects, for every lattice and kind of failure, and
+    # leaves the chain's state as it was
+    import torch
+
+    def put(a):
+        return a if where == "host" else torch.from_numpy(a).cuda()
+
+    cases = []
+    st = O.aztec(12)
+    b = st.copy(); b[0, 3, 7] = 2; cases.append(("aztec", (12,), st, b, "byte"))
+    b = st.copy(); b[0, 12, 12] ^= 1; cases.append(("aztec", (12,), st, b, "face"))
+    b = st.copy(); b[0, 5, st.shape[2] - 1] = 1; cases.append(("aztec", (12,), st, b, "edge outside"))
+    hx = O.hexagon(6, 7, 5)
+    b = hx.copy(); b[1, 4, 4] ^= 1; cases.append(("hexagon", (6, 7, 5), hx, b, "lozenge"))
+    dw = O.dwbc(9)
+    b = dw.copy(); b[0, 4, 4] ^= 1; cases.append(("dwbc", (9,), dw, b, "six-vertex"))
+    b = dw.copy(); b[1, 0, 3] ^= 1; cases.append(("dwbc", (9,), dw, b, "six-vertex"))
+    b = dw.copy(); b[0, 0, dw.shape[2] - 1] = 1; cases.append(("dwbc", (9,), dw, b, "six-vertex"))
+    for kind, args, good, bad, word in cases:
+        dom = getattr(T.Domain, kind)(*args)
+        th = T.thresholds(table16=O.sixv_thresholds([1] * 6)) if kind == "dwbc" else T.thresholds(scalar=1 << 31)
+        ch = T.Chain(ctx, dom, seed=2, th=th)
+        ch.run(7)
+        before = ch.state_hash()
+        with pytest.raises(T.TilingError):
+            T.Chain(ctx, dom, seed=2, th=th, init=bad)       # host validation
+        msg = _reject(T, ch, put(bad))                       # device validation
+        assert word in msg, (kind, msg)
+        assert ch.state_hash() == before
+        ch.write_state(put(good))
+        assert ch.state_hash() == O.state_hash(good)
