@@ -174,14 +174,30 @@ TL_DEV uint4 heat_bath(uint4 f, int kmax, const RndPre& rnd, const TB& tb)
     uint4 lt = make_uint4(0u, 0u, 0u, 0u);
     const int kp = (kmax + 1) < rnd.npre ? (kmax + 1) : rnd.npre;
     int k = 0;
+    // Planes are compared in small blocks whose loads and draws are issued
+    // together: comparing a plane after every site is decided changes
+    // nothing (the undecided mask is then zero), so only the latency of the
+    // chain changes, not the result.
+    for (; k + 4 <= kp; k += 4) {
+        if (!any4(und)) return lt;
+        const uint4 p0 = rnd.pre[(size_t)k * rnd.stride], p1 = rnd.pre[(size_t)(k + 1) * rnd.stride],
+                    p2 = rnd.pre[(size_t)(k + 2) * rnd.stride], p3 = rnd.pre[(size_t)(k + 3) * rnd.stride];
+        hb_compare(lt, und, p0, tb(k));
+        hb_compare(lt, und, p1, tb(k + 1));
+        hb_compare(lt, und, p2, tb(k + 2));
+        hb_compare(lt, und, p3, tb(k + 3));
+    }
     for (; k < kp; ++k) {
         if (!any4(und)) return lt;
         hb_compare(lt, und, rnd.pre[(size_t)k * rnd.stride], tb(k));
     }
-    for (; k <= kmax; ++k) {
-        if (!any4(und)) break;
-        hb_compare(lt, und, rnd.more(k), tb(k));
+    for (; k + 1 <= kmax; k += 2) {
+        if (!any4(und)) return lt;
+        const uint4 o0 = rnd.more(k), o1 = rnd.more(k + 1);
+        hb_compare(lt, und, o0, tb(k));
+        hb_compare(lt, und, o1, tb(k + 1));
     }
+    if (k <= kmax && any4(und)) hb_compare(lt, und, rnd.more(k), tb(k));
     return lt;
 }
 
