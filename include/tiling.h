@@ -293,7 +293,10 @@ uint64_t tl_chain_sweep(const tl_chain* c);
  * 0xFFFF0000 | i, stream_id)), and the site draws of that slot use pass
  * field i.  Every pass preserves the Gibbs measure, so both orders sample
  * it.  Chains with the random order cannot join a batch (TL_EUNSUPPORTED
- * there).  Errors: TL_EINVAL. */
+ * there).  Choosing TL_ORDER_RANDOM waits for the device once and allocates
+ * the chain's buffer of slot colours (3.84 MB, enough for any launch), so
+ * tl_run_sweeps still only enqueues.  Errors: TL_EINVAL, TL_ENOMEM,
+ * TL_ECUDA. */
 #define TL_ORDER_FIXED 0
 #define TL_ORDER_RANDOM 1
 int tl_chain_set_order(tl_chain* c, int order);

@@ -1717,6 +1717,11 @@ static bool want_resident(tl_chain* c)
     return c->res_ready;
 }
 
+// Pass slots of one resident launch at most: exchange tags carry 16 bits of
+// cycle, so a launch runs at most 60,000 cycles, each of at most 64 passes
+// (the largest halo a plan takes).
+constexpr size_t kMaxLaunchSlots = (size_t)60000 * 64;
+
 // Resident launches over [c->sweep, c->sweep + k), at most spl sweeps each.
 static int run_resident(tl_chain* c, uint64_t k, unsigned long long* ring, void* stream)
 {
@@ -2119,6 +2124,18 @@ TL_API int tl_aztec_shuffle(tl_ctx* ctx, int n, uint64_t seed, uint32_t stream_i
 TL_API int tl_chain_set_order(tl_chain* c, int order)
 {
     if (!c || (order != TL_ORDER_FIXED && order != TL_ORDER_RANDOM)) return fail(TL_EINVAL, "tl_chain_set_order: bad argument");
+    // the colours of one resident launch's pass slots: at most 60,000
+    // exchange cycles of at most 64 passes per launch, sized here once so
+    // that tl_run_sweeps only enqueues
+    if (order == TL_ORDER_RANDOM && c->colours_cap < kMaxLaunchSlots) {
+        CUDA_TRY(cudaSetDevice(c->ctx->device));
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(c->colours);
+        c->colours = nullptr;
+        c->colours_cap = 0;
+        TL_TRY(dev_alloc(&c->colours, kMaxLaunchSlots, "pass colours"));
+        c->colours_cap = kMaxLaunchSlots;
+    }
     c->random_order = order == TL_ORDER_RANDOM;
     return TL_OK;
 }
