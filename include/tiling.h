@@ -546,6 +546,12 @@ typedef struct {
     int grid;               /* out: CTAs per launch */
     int smem_bytes;         /* out: dynamic shared memory per CTA */
     int ntiles;             /* out: tiles in the work list */
+    int threads;            /* threads per tile, 256 or 128 (0 = keep; default
+                               256): a thread takes every threads-th 128-face
+                               group of a pass, so this sets the faces per
+                               thread (128 threads: twice as many, with more
+                               tiles resident per SM where shared memory
+                               allows) */
 } tl_batch_plan;
 
 int tl_batch_create(tl_ctx* ctx, tl_chain* const* chains, size_t n, tl_batch** out);
@@ -566,8 +572,9 @@ int tl_batch_run_per_chain(tl_batch* b, uint64_t k, void* stream);
 int tl_batch_hashes(tl_batch* b, uint64_t* out, size_t n, void* stream);
 int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* plan);
 int tl_batch_get_plan(tl_batch* b, tl_batch_plan* plan);
-/* Time every tile height in {32, 64, 128} x R in {1, 2, 4, 8} on the batch
- * itself for `trial_sweeps` sweeps (rounded up to a multiple of R), twice
+/* Time every tile height in {32, 64, 128} x R in {1, 2, 4, 8} x threads per
+ * tile in {256, 128} (the faces per thread) on the batch itself for
+ * `trial_sweeps` sweeps (rounded up to a multiple of R), twice
  * each from the same states, and keep the plan with the fastest run; states
  * and sweep counters are restored afterwards.  The result is cached per
  * (lattices present, threshold kinds present, total rows rounded down to a

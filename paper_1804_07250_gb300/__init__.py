@@ -65,7 +65,7 @@ class Plan(ctypes.Structure):
 class BatchPlan(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int), ("sweeps_per_launch", ctypes.c_int),
                 ("graph_block", ctypes.c_int), ("grid", ctypes.c_int), ("smem_bytes", ctypes.c_int),
-                ("ntiles", ctypes.c_int)]
+                ("ntiles", ctypes.c_int), ("threads", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -584,8 +584,8 @@ class Batch:
         _check(_lib.tl_batch_hashes(self._h, p, n // 8, _stream(stream)))
         return out
 
-    def set_plan(self, tile_rows=0, sweeps_per_launch=0, graph_block=0):
-        p = BatchPlan(tile_rows, sweeps_per_launch, graph_block, 0, 0, 0)
+    def set_plan(self, tile_rows=0, sweeps_per_launch=0, graph_block=0, threads=0):
+        p = BatchPlan(tile_rows, sweeps_per_launch, graph_block, 0, 0, 0, threads)
         _check(_lib.tl_batch_set_plan(self._h, ctypes.byref(p)))
 
     def plan(self) -> dict:

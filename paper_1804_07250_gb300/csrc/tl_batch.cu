@@ -111,14 +111,19 @@ TL_DEV void tile_passes(const BatchChain& ch, uint32_t* srow0, int slo, int shi,
     }
 }
 
-// Three CTAs per SM (at most 80 registers a thread): the passes of a tile are
-// separated by barriers, and a third resident tile hides them better than
-// the registers spilled to L1 cost (two CTAs at 124 registers measured 9%
-// slower, four at 64 registers no faster).
-__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchChain* __restrict__ chains,
-                                                    const BatchTile* __restrict__ tiles, int ntiles, int R,
-                                                    uint32_t sweep_off, int src, unsigned int* cursor,
-                                                    int* __restrict__ status)
+// NT threads per tile: a thread takes every NT-th 128-face group of a pass
+// (the faces per thread the autotuner picks).  256 threads: three CTAs per
+// SM (at most 85 registers a thread): the passes of a tile are separated by
+// barriers, and a third resident tile hides them better than the registers
+// spilled to L1 cost (two CTAs at 124 registers measured 9% slower, four at
+// 64 registers no faster).  128 threads: six CTAs per SM at the same
+// registers, twice the faces per thread, as many tiles as shared memory
+// holds.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) batch_kernel(const BatchChain* __restrict__ chains,
+                                                                    const BatchTile* __restrict__ tiles, int ntiles,
+                                                                    int R, uint32_t sweep_off, int src,
+                                                                    unsigned int* cursor, int* __restrict__ status)
 {
     extern __shared__ uint4 smem4[];
     __shared__ int s_tile;
@@ -206,23 +211,33 @@ __global__ void batch_advance_kernel(const BatchChain* __restrict__ chains, int 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncursors; i += gridDim.x * blockDim.x) cursors[i] = 0u;
 }
 
-int batch_prepare(size_t smem_bytes, int* blocks_per_sm)
+static const void* batch_pick(int threads)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return threads == 128 ? reinterpret_cast<const void*>(&batch_kernel<128>)
+                          : reinterpret_cast<const void*>(&batch_kernel<256>);
+}
+
+int batch_prepare(size_t smem_bytes, int threads, int* blocks_per_sm)
+{
+    const void* k = batch_pick(threads);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return (int)e;
     }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, 256, smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads == 128 ? 128 : 256, smem_bytes);
     if (e != cudaSuccess) cudaGetLastError();
     return (int)e;
 }
 
 int launch_batch(const BatchChain* chains, const BatchTile* tiles, int ntiles, int R, uint32_t sweep_off, int src,
-                 unsigned int* cursor, int grid, size_t smem_bytes, int* status, void* stream)
+                 unsigned int* cursor, int grid, int threads, size_t smem_bytes, int* status, void* stream)
 {
-    batch_kernel<<<grid, 256, smem_bytes, reinterpret_cast<cudaStream_t>(stream)>>>(chains, tiles, ntiles, R,
-                                                                                   sweep_off, src, cursor, status);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (threads == 128)
+        batch_kernel<128><<<grid, 128, smem_bytes, st>>>(chains, tiles, ntiles, R, sweep_off, src, cursor, status);
+    else
+        batch_kernel<256><<<grid, 256, smem_bytes, st>>>(chains, tiles, ntiles, R, sweep_off, src, cursor, status);
     return (int)cudaGetLastError();
 }
 

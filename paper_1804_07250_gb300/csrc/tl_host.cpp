@@ -2514,6 +2514,7 @@ struct tl_batch {
     unsigned long long* d_hash = nullptr;
     int* d_status = nullptr;              // raised by a bounded wait that gave up
     int tile_rows = 64, R = 2, block = 100, grid = 0;
+    int threads = 256;                    // threads per tile (faces per thread)
     size_t smem = 0;
     int ntiles = 0;
     int src = 0;                          // buffer holding the current state
@@ -2558,9 +2559,10 @@ static void batch_free(tl_batch* b)
 }
 
 // Tiles of height tile_rows for every chain; shared memory for tile + halo.
-static int batch_plan(tl_batch* b, int tile_rows, int R)
+static int batch_plan(tl_batch* b, int tile_rows, int R, int threads)
 {
-    if (tile_rows < 1 || R < 1 || R > 64) return fail(TL_EINVAL, "batch plan: tile_rows %d, R %d", tile_rows, R);
+    if (tile_rows < 1 || R < 1 || R > 64 || (threads != 128 && threads != 256))
+        return fail(TL_EINVAL, "batch plan: tile_rows %d, R %d, threads %d", tile_rows, R, threads);
     std::vector<BatchTile> tiles;
     std::vector<double> work;
     std::vector<int> first;
@@ -2586,7 +2588,8 @@ static int batch_plan(tl_batch* b, int tile_rows, int R)
     first.push_back((int)tiles.size());
     if ((long)smem > (long)b->ctx->smem_optin) return fail(TL_EUNSUPPORTED, "batch plan: a tile needs %zu B of shared memory", smem);
     int bps = 0;
-    if (batch_prepare(smem, &bps) != 0 || bps < 1) return fail(TL_EUNSUPPORTED, "batch plan: tile kernel does not fit");
+    if (batch_prepare(smem, threads, &bps) != 0 || bps < 1)
+        return fail(TL_EUNSUPPORTED, "batch plan: tile kernel does not fit");
     std::vector<int> order(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
@@ -2603,6 +2606,7 @@ static int batch_plan(tl_batch* b, int tile_rows, int R)
     b->ntiles = (int)tiles.size();
     b->tile_rows = tile_rows;
     b->R = R;
+    b->threads = threads;
     b->smem = smem;
     b->grid = std::min(bps * b->ctx->sms, b->ntiles);
     return TL_OK;
@@ -2647,7 +2651,7 @@ static int batch_rebuild(tl_batch* b)
     if (n) CUDA_TRY(cudaMemcpy(b->d_chains, b->hchains.data(), sizeof(BatchChain) * n, cudaMemcpyHostToDevice));
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
-    if (n) return batch_plan(b, b->tile_rows, b->R);
+    if (n) return batch_plan(b, b->tile_rows, b->R, b->threads);
     b->ntiles = 0;
     return TL_OK;
 }
@@ -2745,8 +2749,8 @@ static int batch_launch(tl_batch* b, int r, uint32_t off, int slot, void* stream
     unsigned int* cur = b->d_cursor + (slot % b->ncursor);
     if (!per_chain) {
         CUDA_TRY(cudaMemsetAsync(cur, 0, 4, SS(stream)));
-        const int e = launch_batch(b->d_chains, b->d_tiles_lpt, b->ntiles, r, off, b->src, cur, b->grid, b->smem,
-                                   b->d_status, stream);
+        const int e = launch_batch(b->d_chains, b->d_tiles_lpt, b->ntiles, r, off, b->src, cur, b->grid, b->threads,
+                                   b->smem, b->d_status, stream);
         if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
         b->launches += 1;
     } else {
@@ -2755,7 +2759,7 @@ static int batch_launch(tl_batch* b, int r, uint32_t off, int slot, void* stream
             unsigned int* ci = b->d_cursor + ((slot * (int)b->chains.size() + (int)i) % b->ncursor);
             CUDA_TRY(cudaMemsetAsync(ci, 0, 4, SS(stream)));
             const int e = launch_batch(b->d_chains, b->d_tiles_chain + t0, nt, r, off, b->src, ci,
-                                       std::min(nt, b->grid), b->smem, b->d_status, stream);
+                                       std::min(nt, b->grid), b->threads, b->smem, b->d_status, stream);
             if (e) return fail(TL_ECUDA, "batch kernel: %s", cudaGetErrorString((cudaError_t)e));
             b->launches += 1;
         }
@@ -2910,6 +2914,7 @@ TL_API int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* p)
     CUDA_TRY(cudaSetDevice(b->ctx->device));
     const int tr = p->tile_rows > 0 ? p->tile_rows : b->tile_rows;
     const int R = p->sweeps_per_launch > 0 ? p->sweeps_per_launch : b->R;
+    const int nt = p->threads > 0 ? p->threads : b->threads;
     if (p->graph_block > 0) {
         b->block = p->graph_block;
         b->no_graph = false;
@@ -2917,7 +2922,7 @@ TL_API int tl_batch_set_plan(tl_batch* b, const tl_batch_plan* p)
         b->no_graph = true;
     }
     CUDA_TRY(cudaDeviceSynchronize());
-    return batch_plan(b, tr, R);
+    return batch_plan(b, tr, R, nt);
 }
 
 TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
@@ -2929,6 +2934,7 @@ TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
     p->grid = b->grid;
     p->smem_bytes = (int)b->smem;
     p->ntiles = b->ntiles;
+    p->threads = b->threads;
     return TL_OK;
 }
 
@@ -2941,7 +2947,10 @@ TL_API int tl_batch_get_plan(tl_batch* b, tl_batch_plan* p)
 namespace {
 using TuneKey = std::tuple<int, int, int, int>;
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // -> (tile rows, sweeps per launch)
+struct TunePlan {
+    int tile_rows, R, threads;
+};
+std::map<TuneKey, TunePlan> g_tune_cache;   // -> the plan the trials chose
 TuneKey tune_key(const tl_batch* b)
 {
     int lat = 0, thr = 0;
@@ -2975,7 +2984,8 @@ TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, t
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end() && batch_plan(b, it->second.first, it->second.second) == TL_OK) {
+        if (it != g_tune_cache.end() &&
+            batch_plan(b, it->second.tile_rows, it->second.R, it->second.threads) == TL_OK) {
             if (out) TL_TRY(tl_batch_get_plan(b, out));
             return TL_OK;
         }
@@ -2994,16 +3004,18 @@ TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, t
     for (auto* c : b->chains) sweeps.push_back(c->sweep);
     const int tile_opts[] = {32, 64, 128};
     const int r_opts[] = {1, 2, 4, 8};
+    const int nt_opts[] = {256, 128};
     float best = 1e30f;
-    int best_t = b->tile_rows, best_r = b->R;
+    int best_t = b->tile_rows, best_r = b->R, best_nt = b->threads;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = TL_OK;
+    for (int nt : nt_opts)
     for (int tr : tile_opts)
         for (int R : r_opts) {
             if (rc != TL_OK) break;
-            if (batch_plan(b, tr, R) != TL_OK) continue;   // does not fit: skip
+            if (batch_plan(b, tr, R, nt) != TL_OK) continue;   // does not fit: skip
             const uint64_t k = ((trial_sweeps + R - 1) / R) * R;
             const int saved_block = b->block;
             b->block = 1 << 30;                            // no graph during trials
@@ -3036,6 +3048,7 @@ TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, t
                 best = ms / k;
                 best_t = tr;
                 best_r = R;
+                best_nt = nt;
             }
             // restore
             o = 0;
@@ -3051,10 +3064,10 @@ TL_API int tl_batch_autotune(tl_batch* b, uint64_t trial_sweeps, void* stream, t
     cudaEventDestroy(e1);
     cudaFree(snap);
     if (rc != TL_OK) return rc;
-    TL_TRY(batch_plan(b, best_t, best_r));
+    TL_TRY(batch_plan(b, best_t, best_r, best_nt));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = std::make_pair(best_t, best_r);
+        g_tune_cache[key] = TunePlan{best_t, best_r, best_nt};
     }
     if (out) TL_TRY(tl_batch_get_plan(b, out));
     return TL_OK;

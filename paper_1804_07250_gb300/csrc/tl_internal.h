@@ -167,10 +167,11 @@ struct BatchChain {
 struct BatchTile {
     int chain, lo, hi;          // owned rows [lo, hi) of chain `chain`
 };
-int batch_prepare(size_t smem_bytes, int* blocks_per_sm);
+// threads per tile: 256 or 128
+int batch_prepare(size_t smem_bytes, int threads, int* blocks_per_sm);
 // status: device int raised if a bounded wait for a tile's bulk copy gave up.
 int launch_batch(const BatchChain* chains, const BatchTile* tiles, int ntiles, int R, uint32_t sweep_off, int src,
-                 unsigned int* cursor, int grid, size_t smem_bytes, int* status, void* stream);
+                 unsigned int* cursor, int grid, int threads, size_t smem_bytes, int* status, void* stream);
 // advance every chain's sweep counter by k and zero the launch cursors
 int launch_batch_advance(const BatchChain* chains, int nchains, uint32_t k, unsigned int* cursors, int ncursors,
                          void* stream);

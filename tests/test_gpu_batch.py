@@ -67,14 +67,16 @@ def _oracle(spec, stream_id, k):
     return st
 
 
-@pytest.mark.parametrize("tile_rows,R,block,per_chain", [
-    (64, 2, 100, False), (8, 1, 100, False), (16, 3, 6, False), (32, 4, 8, False), (5, 2, 100, True)])
-def test_batch_matches_alone_and_oracle(T, ctx, tile_rows, R, block, per_chain):
+@pytest.mark.parametrize("tile_rows,R,block,per_chain,threads", [
+    (64, 2, 100, False, 256), (8, 1, 100, False, 256), (16, 3, 6, False, 256), (32, 4, 8, False, 256),
+    (5, 2, 100, True, 256), (64, 2, 100, False, 128), (16, 3, 6, False, 128), (5, 2, 100, True, 128)])
+def test_batch_matches_alone_and_oracle(T, ctx, tile_rows, R, block, per_chain, threads):
     import torch
     specs = _specs()
     chains = [_make(T, ctx, sp, 100 + i) for i, sp in enumerate(specs)]
     b = T.Batch(ctx, chains)
-    b.set_plan(tile_rows, R, block)
+    b.set_plan(tile_rows, R, block, threads)
+    assert b.plan()["threads"] == threads
     stream = torch.cuda.Stream()
     k1, k2 = 13, 24
     (b.run_per_chain if per_chain else b.run)(k1, stream=stream)
