@@ -110,21 +110,23 @@ TL_DEV void store_shr(uint32_t* p, uint4 raw, uint4 fl, int k0, int K)
 // counter (group, sweep, (k << 16) | pass, stream), supplied by `rnd`.  It
 // stops once no flippable site is undecided, or after plane kmax, beyond
 // which every remaining threshold bit is zero (so an undecided u is >= t).
+TL_DEV void hb_compare(uint4& lt, uint4& und, uint4 o, uint4 t);
 template <class RND, class TB>
 TL_DEV uint4 heat_bath(uint4 f, int kmax, const RND& rnd, const TB& tb)
 {
     uint4 und = f;
     uint4 lt = make_uint4(0u, 0u, 0u, 0u);
-    for (int k = 0; k <= kmax; ++k) {
-        if (!any4(und)) break;
-        const uint4 o = rnd(k);
-        const uint4 t = tb(k);
-        uint32_t d;
-        d = o.x ^ t.x; lt.x |= und.x & d & t.x; und.x &= ~d;
-        d = o.y ^ t.y; lt.y |= und.y & d & t.y; und.y &= ~d;
-        d = o.z ^ t.z; lt.z |= und.z & d & t.z; und.z &= ~d;
-        d = o.w ^ t.w; lt.w |= und.w & d & t.w; und.w &= ~d;
+    // planes drawn two at a time (a plane compared after every site is
+    // decided changes nothing)
+    int k = 0;
+    for (; k + 1 <= kmax; k += 2) {
+        if (!any4(und)) return lt;
+        const uint4 o0 = rnd(k), o1 = rnd(k + 1);
+        const uint4 t0 = tb(k), t1 = tb(k + 1);
+        hb_compare(lt, und, o0, t0);
+        hb_compare(lt, und, o1, t1);
     }
+    if (k <= kmax && any4(und)) hb_compare(lt, und, rnd(k), tb(k));
     return lt;
 }
 
