@@ -154,6 +154,44 @@ TL_DEV uint32_t unpack61(const unsigned long long (&f)[kXFields], int j)
     return (uint32_t)x;
 }
 
+// A density sample of one row pair: its eight 4-word blocks (rows y0 and
+// y0 + 1, planes He, Ho, Ve, Vo; block j at counter word i0 + (j / 4) RW +
+// (j % 4) K) are added to the bit-sliced counters together, counter plane
+// by counter plane.  All reads of a plane are issued before any write, so a
+// sample is one chain of dependent counter accesses, as long as the longest
+// carry, instead of one chain per block.  J blocks from j0 at a time: all
+// eight, or (the 512-thread build, short of registers) one row's four.
+template <int J>
+TL_DEV void pair_count_sliced(const PairWords& pw, int j0, int64_t i0, int64_t RW, int K, int64_t plane_words,
+                              uint32_t* cplanes)
+{
+#ifdef TL_DEBUG
+    if (!TL_IN(i0 + ((j0 + J - 1) >> 2) * RW + 3 * (int64_t)K + 3, plane_words, 107)) return;
+#endif
+    uint4 carry[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) carry[j] = pw.v[j0 + j];
+    for (int b = 0; b < 32; ++b) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < J; ++j) any |= any4(carry[j]);
+        if (!any) break;
+        uint32_t* const base = cplanes + (int64_t)b * plane_words + i0;
+        uint4 c[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            c[j] = any4(carry[j]) ? *reinterpret_cast<const uint4*>(base + ((j0 + j) >> 2) * RW + ((j0 + j) & 3) * K)
+                                  : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (any4(carry[j])) {
+                *reinterpret_cast<uint4*>(base + ((j0 + j) >> 2) * RW + ((j0 + j) & 3) * K) = x4(c[j], carry[j]);
+                carry[j] = make_uint4(carry[j].x & c[j].x, carry[j].y & c[j].y, carry[j].z & c[j].z,
+                                      carry[j].w & c[j].w);
+            }
+    }
+}
+
 // COUNT: the chain counts its accepted flips (a separate instantiation, so
 // the default path carries no counter).  RND: the colour of every pass slot
 // comes from the host's table (random order) instead of slot s updating
@@ -349,21 +387,28 @@ __global__ void __launch_bounds__(NT, 1) regdom_kernel(const RegParams P)
                 uint64_t acc = 0;
                 if (owned) {
                     const PairWords pw{{He0, Ho0, Ve0, Vo0, He1, Ho1, Ve1, Vo1}};
+                    if (sample) {
+                        const int64_t i0 = (int64_t)y0 * RW + k0, pw_ = (int64_t)g.H * RW;
+                        if (NT < 512 && y0 + 1 < g.H) {
+                            pair_count_sliced<8>(pw, 0, i0, RW, K, pw_, P.counts);
+                        } else {
+                            pair_count_sliced<4>(pw, 0, i0, RW, K, pw_, P.counts);
+                            if (y0 + 1 < g.H) pair_count_sliced<4>(pw, 4, i0, RW, K, pw_, P.counts);
+                        }
+                    }
+                    if (P.ring) {
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const int y = y0 + r;
-                        if (y >= g.H) continue;
+                        for (int r = 0; r < 2; ++r) {
+                            const int y = y0 + r;
+                            if (y >= g.H) continue;
 #pragma unroll
-                        for (int pl = 0; pl < 4; ++pl) {
-                            const uint4 v4 = pw.v[4 * r + pl];
-                            if (sample && any4(v4))
-                                word_count_sliced4(v4, (int64_t)y * RW + (int64_t)pl * K + k0,
-                                                   (int64_t)g.H * RW, P.counts);
-                            if (!P.ring) continue;
-                            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                            for (int pl = 0; pl < 4; ++pl) {
+                                const uint4 v4 = pw.v[4 * r + pl];
+                                const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                            for (int w = 0; w < 4; ++w)
-                                if (vv[w]) acc += word_hash(vv[w], g, y, pl, k0 + w);
+                                for (int w = 0; w < 4; ++w)
+                                    if (vv[w]) acc += word_hash(vv[w], g, y, pl, k0 + w);
+                            }
                         }
                     }
                 }

@@ -130,6 +130,33 @@ def test_density_and_nsew(T, ctx):
     assert np.array_equal(np.rint(ch.read_nsew() * nsamp).astype(np.uint32), ncounts)
 
 
+@pytest.mark.parametrize("shape,halo,min_threads", [(("aztec", 100), 0, 0), (("aztec", 129), 4, 0),
+                                                    (("rect", 9000, 30), 8, 385)])
+def test_density_many_samples(T, ctx, shape, halo, min_threads):
+    # a sample after every sweep for 300 sweeps, so the bit-sliced counters
+    # carry through nine planes; both ways the kernel adds a pair's blocks
+    # (all eight at once, or row by row in the 512-thread build) and the
+    # odd last vertex row of the box must count exactly what the oracle does
+    if shape[0] == "aztec":
+        dom, st = T.Domain.aztec(shape[1]), O.aztec(shape[1])
+    else:
+        dom, st = T.Domain.rect(shape[1], shape[2]), O.rect(shape[1], shape[2])
+    ch = T.Chain(ctx, dom, seed=6, th=T.thresholds(scalar=T_HALF), init=st.copy())
+    ch.set_plan(3, 0, halo)
+    plan = ch.plan()
+    assert plan["kernel"] == 3 and plan["threads"] >= min_threads, plan
+    ch.density_begin(stride=1, burn_in=0)
+    ch.run(300)
+    dens, samples = ch.read_density()
+    counts = np.zeros(st.shape, dtype=np.uint32)
+    for s in range(300):
+        O.sweeps(O.DOMINO, st, seed=6, sweep0=s, k=1, t_scalar=T_HALF)
+        O.accumulate(st, counts)
+    assert samples == 300
+    assert np.array_equal(np.rint(dens * 300).astype(np.uint32), counts)
+    assert np.array_equal(ch.read_state(), st)
+
+
 def test_kernels_agree_at_full_size(T, ctx):
     # the register-resident and the shared-memory resident kernels give the
     # same chain on the benchmark domain (Aztec 2048), 300 sweeps
