@@ -41,3 +41,51 @@ def gather_results(obj, dist=None) -> list:
     out = [None] * dist.get_world_size()
     dist.all_gather_object(out, obj)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Liveness between steps
+#
+# A rank that raised, exited or never joined is found on the host, through a
+# key-value store the ranks share (any torch.distributed Store: the process
+# group's TCPStore, a FileStore), before the next launch or collective:
+# every rank records each step it finished, and before starting the next one
+# waits, with a short limit, until every other rank has recorded it.  The
+# surviving ranks then learn which ranks were lost instead of waiting inside
+# a collective for a peer that will never arrive; their own chains and
+# results are untouched.
+# ---------------------------------------------------------------------------
+
+
+class PeerLost(RuntimeError):
+    """Ranks that did not record a step within the liveness limit."""
+
+    def __init__(self, step: int, ranks):
+        self.step = int(step)
+        self.ranks = sorted(int(r) for r in ranks)
+        super().__init__("rank(s) %s did not finish step %d" % (", ".join(map(str, self.ranks)), self.step))
+
+
+def _step_key(step: int, rank: int) -> str:
+    return "tl/step/%d/%d" % (step, rank)
+
+
+def heartbeat(store, rank: int, step: int) -> None:
+    """Record in `store` that `rank` finished `step`: its work for the step is
+    complete and nothing of it is still in flight."""
+    store.set(_step_key(step, rank), b"1")
+
+
+def wait_peers(store, world: int, step: int, timeout_s: float, poll_s: float = 0.01) -> None:
+    """Return once every rank of `world` has recorded `step`; raise PeerLost
+    naming the ranks that have not after `timeout_s` seconds."""
+    import time
+    keys = [_step_key(step, r) for r in range(world)]
+    deadline = time.monotonic() + float(timeout_s)
+    while True:
+        missing = [r for r, k in enumerate(keys) if not store.check([k])]
+        if not missing:
+            return
+        if time.monotonic() >= deadline:
+            raise PeerLost(step, missing)
+        time.sleep(poll_s)

@@ -98,3 +98,84 @@ def test_bench_starts_its_own_ranks():
     assert len(lines) == 1, r.stdout
     out = json.loads(lines[0])
     assert out["n_gpus"] == 2 and out["ranks_seen"] == 2 and out["distinct_streams"] == 2
+
+
+def _liveness_worker(rank, world, port, out_dir, lost_rank):
+    # three steps of a replica chain; after each, the rank records the step
+    # and waits (3 s at most) for every other rank to record it before going on
+    import datetime
+    import json
+    import time
+
+    import torch.distributed as dist
+
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=datetime.timedelta(seconds=60))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    import oracle as O
+    from paper_1804_07250_gb300 import replicas as R
+
+    st = O.aztec(6)
+    done, lost, total, waited = 0, None, None, 0.0
+    try:
+        for step in range(3):
+            if rank == lost_rank and step == 1:
+                raise RuntimeError("injected failure before the end of step 1")
+            O.sweeps(O.DOMINO, st, seed=9, stream=R.replica_stream_id(0, rank, world), sweep0=5 * step, k=5,
+                     t_scalar=1 << 31)
+            done = step + 1
+            R.heartbeat(store, rank, step)
+            t0 = time.monotonic()
+            try:
+                R.wait_peers(store, world, step, timeout_s=3.0)
+            finally:
+                waited = time.monotonic() - t0
+        total = R.max_over_ranks(float(done), dist)   # the collective after the last step
+    except R.PeerLost as e:
+        lost = {"step": e.step, "ranks": e.ranks}
+    except RuntimeError:
+        if rank == lost_rank:
+            os._exit(3)   # the failed rank leaves without touching the group again
+        raise
+    with open(os.path.join(out_dir, "live%d.json" % rank), "w") as f:
+        json.dump({"done": done, "lost": lost, "total": total, "waited": waited, "hash": int(O.state_hash(st))}, f)
+    if lost is None:
+        dist.destroy_process_group()
+    os._exit(0)
+
+
+@pytest.mark.parametrize("lost_rank", [None, 1])
+def test_lost_rank_is_found_between_steps(tmp_path, lost_rank):
+    # a rank that fails between steps is found by the others on the host,
+    # through the shared store, within the liveness limit: they stop before
+    # the next collective (none waits for the lost rank) and keep their own
+    # results; with no failure every step and the final collective complete
+    import json
+    import multiprocessing
+
+    import oracle as O
+
+    world, port = 2, _free_port()
+    ctx = multiprocessing.get_context("spawn")
+    procs = [ctx.Process(target=_liveness_worker, args=(r, world, port, str(tmp_path), lost_rank))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    codes = [p.exitcode for p in procs]
+    for p in procs:
+        if p.exitcode is None:
+            p.kill()
+    assert codes[0] == 0, codes
+    out0 = json.load(open(tmp_path / "live0.json"))
+    st = O.aztec(6)
+    O.sweeps(O.DOMINO, st, seed=9, stream=0, k=5 * out0["done"], t_scalar=1 << 31)
+    assert out0["hash"] == O.state_hash(st)       # the survivor's chain is exact
+    if lost_rank is None:
+        assert codes == [0, 0]
+        assert out0["done"] == 3 and out0["lost"] is None and out0["total"] == 3.0
+    else:
+        assert codes[1] == 3
+        assert out0["done"] == 2 and out0["total"] is None
+        assert out0["lost"] == {"step": 1, "ranks": [1]}
+        assert 2.5 < out0["waited"] < 30.0        # found at the limit, not by a hang
