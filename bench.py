@@ -344,8 +344,10 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes_launch / (k_ms / 1e3) / 1e9
     kname, ksrc = RESIDENT_KERNELS.get(plan["kernel"], ("pass_global_kernel", KERNEL_SOURCES))
-    traffic = recorded_traffic(wl["name"], ksrc, {"kernel": plan["kernel"]}) if plan["kernel"] in RESIDENT_KERNELS \
-        else None
+    # the recorded traffic is of the workload's own launches: none for
+    # another sweep count or plan
+    traffic = recorded_traffic(wl["name"], ksrc, {"kernel": plan["kernel"]}) \
+        if plan["kernel"] in RESIDENT_KERNELS and SWEEPS == wl["sweeps"] else None
 
     # end to end through the C-ABI: every step copies its start state in from
     # page-locked host memory and its results (state, heights and, with
